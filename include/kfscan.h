@@ -1,0 +1,160 @@
+/*
+ * kfscan.h -- C ABI of the temporally parallel Kalman filter / smoother
+ * library for NVIDIA GB300 (sm_103a).
+ *
+ * Method: Sarkka & Garcia-Fernandez, "On the Performance of Prefix-Sum
+ * Parallel Kalman Filters and Smoothers on GPUs" (arXiv 2511.10363).
+ * Filtering is the all-prefix-sum of the elements (A,b,C,eta,J) of
+ * Sec. IV-C under the operator of Lemma 1 (Alg. pkf); RTS smoothing is the
+ * reversed all-prefix-sum of the elements (E,g,L) of Sec. IV-D under
+ * Lemma 2 (Alg. prts); two-filter smoothing combines the forward filter with
+ * a reversed all-prefix-sum of (a_2,...,a_T,e) under Lemma 1 and the merge
+ * of Eqs. mean_tf_combination / cov_tf_combination (Alg. ptf).
+ *
+ * Model (Sec. III-A, time-invariant, u = d = 0):
+ *     x_k = F x_{k-1} + q_{k-1}, q ~ N(0,Q);  y_k = H x_k + r_k, r ~ N(0,R);
+ *     x_0 ~ N(m0, P0), i.e. m0 = xbar_{0|0}, P0 = P_{0|0}.
+ *
+ * Conventions shared by every entry point
+ *   - nx in {2, 4, 8}; 1 <= ny <= 8.  Other sizes return KF_ERR_ARG.
+ *   - Model matrices are HOST pointers to row-major FP64 arrays owned by the
+ *     caller and copied during the call: F [nx][nx], Q [nx][nx] symmetric
+ *     positive semi-definite, H [ny][nx], R [ny][ny] symmetric positive
+ *     definite, m0 [nx], P0 [nx][nx] symmetric positive semi-definite.
+ *     R not positive definite, or Q / P0 not symmetric positive
+ *     semi-definite, returns KF_ERR_NOT_PD.
+ *   - Data and result buffers are DEVICE pointers owned by the caller, in
+ *     the working precision: double for KF_FP64, float for KF_FP32 and
+ *     KF_FP32_FP64SOLVE.  y is [T][ny] (y[k-1] is y_k, k = 1..T); means are
+ *     [T][nx]; covariances are full, row-major [T][nx][nx].  Outputs are for
+ *     k = 1..T.  Buffers must not overlap and must be aligned to their
+ *     element size.
+ *   - loglik, when not NULL, is a DEVICE pointer to one double that receives
+ *     log p(y_{1:T}), accumulated in FP64 in a fixed order.
+ *   - workspace: a DEVICE buffer of at least kf_workspace_size(...) bytes,
+ *     256-byte aligned, owned by the caller, used only by this call until it
+ *     completes on the stream.  Passing NULL makes the library use (and grow
+ *     with cudaMalloc) a per-device workspace of its own; calls that use the
+ *     library's workspace must then not run concurrently on different
+ *     streams.
+ *   - stream: a cudaStream_t (NULL = legacy default stream).  Every call is
+ *     asynchronous with respect to the host: it validates its arguments,
+ *     does the k-invariant FP64 precomputation on the host, and enqueues its
+ *     kernels.  Errors detected on the host are returned; errors detected by
+ *     the kernels (a bounded wait that ran out) are recorded in a per-device
+ *     status word read by kf_sync_status().
+ *   - Nothing throws across this boundary.
+ */
+#ifndef KFSCAN_H
+#define KFSCAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Scan algorithm.  DECOUPLED_LOOKBACK is the single-pass scan (one kernel
+ * per scan direction, element construction and extraction fused in);
+ * HILLIS_STEELE, BLELLOCH and LADNER_FISCHER are Algs. 1, 2 and 3 of Sec. II
+ * run level by level over element buffers in device memory (T padded to a
+ * power of two with neutral elements).  AUTO picks the decoupled lookback. */
+typedef enum {
+    KF_SCAN_AUTO = 0,
+    KF_SCAN_DECOUPLED_LOOKBACK = 1,
+    KF_SCAN_HILLIS_STEELE = 2,
+    KF_SCAN_BLELLOCH = 3,
+    KF_SCAN_LADNER_FISCHER = 4
+} kf_scan_t;
+
+/* Working precision.  KF_FP32_FP64SOLVE keeps elements, combines and outputs
+ * in FP32 but forms and inverts every (I + C_i J_j) of Lemma 1 (and the
+ * (I + P J) of the two-filter merge) in FP64 with one step of iterative
+ * refinement. */
+typedef enum { KF_FP64 = 0, KF_FP32 = 1, KF_FP32_FP64SOLVE = 2 } kf_precision_t;
+
+typedef enum {
+    KF_OK = 0,
+    KF_ERR_ARG = 1,      /* bad size, NULL pointer, bad enum, misalignment   */
+    KF_ERR_NOT_PD = 2,   /* R not PD, or Q / P0 not symmetric PSD            */
+    KF_ERR_CUDA = 3,     /* a CUDA runtime call failed                       */
+    KF_ERR_OOM = 4,      /* device allocation failed                         */
+    KF_ERR_TIMEOUT = 5,  /* a bounded inter-block wait in a kernel ran out   */
+    KF_ERR_BUDGET = 6,   /* serving: job larger than the device budget       */
+    KF_ERR_BUSY = 7      /* serving: queue full / unknown job id             */
+} kf_status_t;
+
+typedef struct {
+    int nx, ny;
+    const double *F, *Q, *H, *R, *m0, *P0;   /* host, row-major FP64 */
+} kf_model_t;
+
+/* Human-readable name of a status code (static string). */
+const char *kf_status_string(kf_status_t s);
+
+/* Library version string (static). */
+const char *kf_version(void);
+
+/* Which operation a workspace is sized for. */
+typedef enum { KF_OP_FILTER = 0, KF_OP_RTS = 1, KF_OP_TWO_FILTER = 2 } kf_op_t;
+
+/* Bytes of device workspace needed by one call of the given operation on
+ * total_steps time steps (the sum of the lengths for a batched call). */
+size_t kf_workspace_size(kf_op_t op, int nx, int ny, int64_t total_steps, kf_precision_t prec,
+                         kf_scan_t scan);
+
+/* Parallel Kalman filter, Alg. pkf (Sec. IV-C): filtering means m_out
+ * [T][nx] = xbar_{k|k} and covariances P_out [T][nx][nx] = P_{k|k}.
+ * P_out may be NULL (means only).  T >= 1. */
+kf_status_t kf_filter(const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec,
+                      kf_scan_t scan, void *m_out, void *P_out, double *loglik, void *workspace,
+                      void *stream);
+
+/* Parallel RTS smoother, Alg. prts (Sec. IV-D), including its filter pass:
+ * smoothed ms_out [T][nx] = xbar_{k|T}, Ps_out [T][nx][nx] = P_{k|T}.
+ * mf_out / Pf_out, when not NULL, also receive the filtering results. */
+kf_status_t kf_rts_smooth(const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec,
+                          kf_scan_t scan, void *ms_out, void *Ps_out, void *mf_out, void *Pf_out,
+                          double *loglik, void *workspace, void *stream);
+
+/* Parallel two-filter smoother, Alg. ptf (Secs. IV-E, IV-F), including its
+ * filter pass: same outputs as kf_rts_smooth. */
+kf_status_t kf_two_filter_smooth(const kf_model_t *model, int64_t T, const void *y,
+                                 kf_precision_t prec, kf_scan_t scan, void *ms_out, void *Ps_out,
+                                 void *mf_out, void *Pf_out, double *loglik, void *workspace,
+                                 void *stream);
+
+/* Waits for `stream`, then returns and clears the device status word of the
+ * current device: KF_OK, or KF_ERR_TIMEOUT if some kernel's bounded wait ran
+ * out since the last call (its outputs are then undefined), or KF_ERR_CUDA
+ * if the stream reported an error. */
+kf_status_t kf_sync_status(void *stream);
+
+/* Process-wide options read at the start of every later call.
+ *   KF_OPT_WAIT_TIMEOUT_NS      bound of every inter-CTA wait in the
+ *                               decoupled look-back scan (default 1e9 ns;
+ *                               1e6 .. 6e10 accepted).
+ *   KF_OPT_TEST_SKIP_TILE       test hook: the CTA that takes this tile
+ *                               ticket returns without publishing, so the
+ *                               later tiles' waits run out and the call
+ *                               reports KF_ERR_TIMEOUT (default -1: off).
+ *   KF_OPT_POSITIONS_PER_THREAD time steps folded serially by one thread in
+ *                               the decoupled look-back scan (0 = planner's
+ *                               choice: one wave of resident CTAs).
+ *   KF_OPT_THREADS              CTA size of that scan: 0 (default) or 128.
+ * Returns KF_ERR_ARG for an unknown option or a value out of range. */
+typedef enum {
+    KF_OPT_WAIT_TIMEOUT_NS = 0,
+    KF_OPT_TEST_SKIP_TILE = 1,
+    KF_OPT_POSITIONS_PER_THREAD = 2,
+    KF_OPT_THREADS = 3
+} kf_option_t;
+kf_status_t kf_set_option(kf_option_t opt, int64_t value);
+int64_t kf_get_option(kf_option_t opt); /* -1 for an unknown option */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KFSCAN_H */

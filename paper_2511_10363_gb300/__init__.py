@@ -1,0 +1,196 @@
+"""Python binding of libkfscan (include/kfscan.h): temporally parallel Kalman
+filtering and smoothing as all-prefix-sums (arXiv 2511.10363) on GB300.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch supplies device memory and streams.  The binding refuses
+to run if the compiled library is missing; there is no CPU fallback.
+
+Function names match the C ABI:
+    kf_filter, kf_rts_smooth, kf_two_filter_smooth,
+    kf_workspace_size, kf_sync_status, kf_set_option, kf_get_option,
+    kf_status_string, kf_version.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = _build.LIB
+
+# enums of kfscan.h
+SCANS = {"auto": 0, "dlb": 1, "decoupled_lookback": 1, "hillis_steele": 2, "hs": 2,
+         "blelloch": 3, "ladner_fischer": 4, "lafi": 4}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_fp64solve": 2, "mixed": 2}
+OPS = {"filter": 0, "rts": 1, "two_filter": 2, "tf": 2}
+STATUS = {0: "KF_OK", 1: "KF_ERR_ARG", 2: "KF_ERR_NOT_PD", 3: "KF_ERR_CUDA", 4: "KF_ERR_OOM",
+          5: "KF_ERR_TIMEOUT", 6: "KF_ERR_BUDGET", 7: "KF_ERR_BUSY"}
+OPTIONS = {"wait_timeout_ns": 0, "test_skip_tile": 1, "positions_per_thread": 2, "threads": 3}
+
+_lib = None
+
+
+class KfError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = int(status)
+        super().__init__("%s%s (%d: %s)" % (where + ": " if where else "", STATUS.get(self.status, "?"),
+                                             self.status, kf_status_string(self.status)))
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int)] + [
+        (k, ctypes.POINTER(ctypes.c_double)) for k in ("F", "Q", "H", "R", "m0", "P0")]
+
+
+def lib():
+    """The loaded library.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libkfscan.so is not built: run paper_2511_10363_gb300.build.build() "
+                               "(or __graft_entry__.build()) first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        MP = ctypes.POINTER(_Model)
+        L.kf_filter.argtypes = [MP, i64, vp, i, i, vp, vp, vp, vp, vp]
+        L.kf_rts_smooth.argtypes = [MP, i64, vp, i, i, vp, vp, vp, vp, vp, vp, vp]
+        L.kf_two_filter_smooth.argtypes = [MP, i64, vp, i, i, vp, vp, vp, vp, vp, vp, vp]
+        for f in ("kf_filter", "kf_rts_smooth", "kf_two_filter_smooth", "kf_sync_status", "kf_set_option"):
+            getattr(L, f).restype = ctypes.c_int
+        L.kf_sync_status.argtypes = [vp]
+        L.kf_set_option.argtypes = [i, i64]
+        L.kf_get_option.argtypes = [i]
+        L.kf_get_option.restype = i64
+        L.kf_workspace_size.argtypes = [i, i, i, i64, i, i]
+        L.kf_workspace_size.restype = ctypes.c_size_t
+        L.kf_status_string.argtypes = [i]
+        L.kf_status_string.restype = ctypes.c_char_p
+        L.kf_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def kf_status_string(status: int) -> str:
+    return lib().kf_status_string(int(status)).decode()
+
+
+def kf_version() -> str:
+    return lib().kf_version().decode()
+
+
+class Model:
+    """Host FP64 copy of (F, Q, H, R, m0, P0) laid out for kf_model_t."""
+
+    def __init__(self, model):
+        self.arrays = {k: np.ascontiguousarray(np.asarray(model[k], dtype=np.float64))
+                       for k in ("F", "Q", "H", "R", "m0", "P0")}
+        self.nx = int(self.arrays["F"].shape[0])
+        self.ny = int(self.arrays["H"].shape[0])
+        D = ctypes.POINTER(ctypes.c_double)
+        self.c = _Model(self.nx, self.ny, *[self.arrays[k].ctypes.data_as(D)
+                                             for k in ("F", "Q", "H", "R", "m0", "P0")])
+
+
+def _as_model(model):
+    return model if isinstance(model, Model) else Model(model)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def dtype_of(precision):
+    import torch
+    return torch.float64 if PRECISIONS[precision] == 0 else torch.float32
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise KfError(rc, where)
+
+
+def _prep(model, y, precision):
+    import torch
+    m = _as_model(model)
+    if not (isinstance(y, torch.Tensor) and y.is_cuda):
+        raise TypeError("y must be a CUDA tensor")
+    dt = dtype_of(precision)
+    if y.dtype != dt or not y.is_contiguous() or y.dim() != 2 or y.shape[1] != m.ny:
+        raise ValueError("y must be contiguous [T, ny] of dtype %s" % dt)
+    return m, dt
+
+
+def kf_workspace_size(op, nx, ny, total_steps, precision="fp32", scan="dlb"):
+    return int(lib().kf_workspace_size(OPS[op], nx, ny, int(total_steps), PRECISIONS[precision], SCANS[scan]))
+
+
+def kf_filter(model, y, precision="fp32", scan="dlb", m_out=None, P_out=None, loglik=False,
+              workspace=None, stream=None, want_cov=True):
+    """Alg. pkf.  Returns (m [T,nx], P [T,nx,nx] or None, loglik tensor [1] or None)."""
+    import torch
+    m, dt = _prep(model, y, precision)
+    T = y.shape[0]
+    dev = y.device
+    if m_out is None:
+        m_out = torch.empty((T, m.nx), dtype=dt, device=dev)
+    if P_out is None and want_cov:
+        P_out = torch.empty((T, m.nx, m.nx), dtype=dt, device=dev)
+    ll = torch.empty(1, dtype=torch.float64, device=dev) if loglik else None
+    rc = lib().kf_filter(ctypes.byref(m.c), T, _ptr(y), PRECISIONS[precision], SCANS[scan], _ptr(m_out),
+                         _ptr(P_out), _ptr(ll), _ptr(workspace), _stream(stream))
+    _check(rc, "kf_filter")
+    return m_out, P_out, ll
+
+
+def _smooth(fn, name, model, y, precision, scan, ms_out, Ps_out, mf_out, Pf_out, loglik, workspace, stream):
+    import torch
+    m, dt = _prep(model, y, precision)
+    T = y.shape[0]
+    dev = y.device
+    if ms_out is None:
+        ms_out = torch.empty((T, m.nx), dtype=dt, device=dev)
+    if Ps_out is None:
+        Ps_out = torch.empty((T, m.nx, m.nx), dtype=dt, device=dev)
+    ll = torch.empty(1, dtype=torch.float64, device=dev) if loglik else None
+    rc = fn(ctypes.byref(m.c), T, _ptr(y), PRECISIONS[precision], SCANS[scan], _ptr(ms_out), _ptr(Ps_out),
+            _ptr(mf_out), _ptr(Pf_out), _ptr(ll), _ptr(workspace), _stream(stream))
+    _check(rc, name)
+    return ms_out, Ps_out, ll
+
+
+def kf_rts_smooth(model, y, precision="fp32", scan="dlb", ms_out=None, Ps_out=None, mf_out=None, Pf_out=None,
+                  loglik=False, workspace=None, stream=None):
+    """Alg. prts (with its filter pass).  Returns (ms, Ps, loglik or None)."""
+    return _smooth(lib().kf_rts_smooth, "kf_rts_smooth", model, y, precision, scan, ms_out, Ps_out, mf_out,
+                   Pf_out, loglik, workspace, stream)
+
+
+def kf_two_filter_smooth(model, y, precision="fp32", scan="dlb", ms_out=None, Ps_out=None, mf_out=None,
+                         Pf_out=None, loglik=False, workspace=None, stream=None):
+    """Alg. ptf (with its filter pass).  Returns (ms, Ps, loglik or None)."""
+    return _smooth(lib().kf_two_filter_smooth, "kf_two_filter_smooth", model, y, precision, scan, ms_out,
+                   Ps_out, mf_out, Pf_out, loglik, workspace, stream)
+
+
+def kf_sync_status(stream=None):
+    """Wait for the stream; return the kernels' status (0 = OK) and clear it."""
+    return int(lib().kf_sync_status(_stream(stream)))
+
+
+def kf_set_option(name, value):
+    _check(lib().kf_set_option(OPTIONS[name], int(value)), "kf_set_option")
+
+
+def kf_get_option(name):
+    return int(lib().kf_get_option(OPTIONS[name]))

@@ -1,0 +1,404 @@
+// kf_api.cu -- the C ABI declared in include/kfscan.h: argument checks,
+// the k-invariant FP64 precomputation of Eqs. pkf_init1/2/3 on the host,
+// the per-device workspace cache and status word, and dispatch to the
+// per-state-dimension launch units.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "../../include/kfscan.h"
+#include "kf_host.h"
+
+namespace kfs {
+
+#define KF_PREC_SWITCH(N, prec, F, ...)                          \
+    switch (prec) {                                              \
+        case KF_FP64_I: return F##_n##N##_f64(__VA_ARGS__);      \
+        case KF_FP32_I: return F##_n##N##_f32(__VA_ARGS__);      \
+        default: return F##_n##N##_mix(__VA_ARGS__);             \
+    }
+
+size_t ws_bytes_dispatch(int nx, int op, int prec, int scan, int64_t T) {
+    switch (nx) {
+        case 2: KF_PREC_SWITCH(2, prec, ws_bytes, op, scan, T)
+        case 4: KF_PREC_SWITCH(4, prec, ws_bytes, op, scan, T)
+        case 8: KF_PREC_SWITCH(8, prec, ws_bytes, op, scan, T)
+    }
+    return 0;
+}
+
+cudaError_t launch_dispatch(const LaunchReq &q) {
+    switch (q.hm->n) {
+        case 2: KF_PREC_SWITCH(2, q.prec, launch, q)
+        case 4: KF_PREC_SWITCH(4, q.prec, launch, q)
+        case 8: KF_PREC_SWITCH(8, q.prec, launch, q)
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- small FP64 host algebra
+
+static void mm(int r, int k, int c, const double *A, const double *B, double *C) {
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < c; ++j) {
+            double s = 0;
+            for (int t = 0; t < k; ++t) s += A[i * k + t] * B[t * c + j];
+            C[i * c + j] = s;
+        }
+}
+static void tr(int r, int c, const double *A, double *B) {
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < c; ++j) B[j * r + i] = A[i * c + j];
+}
+// Cholesky of a symmetric matrix; false if not positive definite.
+static bool chol(int n, const double *A, double *L) {
+    for (int i = 0; i < n * n; ++i) L[i] = 0;
+    for (int j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int k = 0; k < j; ++k) s -= L[j * n + k] * L[j * n + k];
+        if (!(s > 0) || !isfinite(s)) return false;
+        L[j * n + j] = sqrt(s);
+        for (int i = j + 1; i < n; ++i) {
+            double u = A[i * n + j];
+            for (int k = 0; k < j; ++k) u -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = u / L[j * n + j];
+        }
+    }
+    return true;
+}
+// inverse and log-determinant of a symmetric positive-definite matrix
+static bool spd_inv(int n, const double *A, double *Ai, double *logdet) {
+    double L[KF_MAXM * KF_MAXM > KF_MAXN * KF_MAXN ? KF_MAXM * KF_MAXM : KF_MAXN * KF_MAXN];
+    if (!chol(n, A, L)) return false;
+    double ld = 0;
+    for (int i = 0; i < n; ++i) ld += 2 * log(L[i * n + i]);
+    if (logdet) *logdet = ld;
+    for (int c = 0; c < n; ++c) {
+        double z[KF_MAXN > KF_MAXM ? KF_MAXN : KF_MAXM], x[KF_MAXN > KF_MAXM ? KF_MAXN : KF_MAXM];
+        for (int i = 0; i < n; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s -= L[i * n + k] * z[k];
+            z[i] = s / L[i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double s = z[i];
+            for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+            x[i] = s / L[i * n + i];
+        }
+        for (int i = 0; i < n; ++i) Ai[i * n + c] = x[i];
+    }
+    return true;
+}
+static bool is_symmetric(int n, const double *A) {
+    double mx = 0;
+    for (int i = 0; i < n * n; ++i) {
+        if (!isfinite(A[i])) return false;
+        mx = fmax(mx, fabs(A[i]));
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+            if (fabs(A[i * n + j] - A[j * n + i]) > 1e-12 * mx) return false;
+    return true;
+}
+// symmetric positive semi-definite: Cholesky of A + delta I with a tiny delta
+static bool is_spsd(int n, const double *A) {
+    if (!is_symmetric(n, A)) return false;
+    double mx = 0, B[KF_MAXN * KF_MAXN], L[KF_MAXN * KF_MAXN];
+    for (int i = 0; i < n * n; ++i) mx = fmax(mx, fabs(A[i]));
+    const double delta = 1e-10 * (mx > 0 ? mx : 1.0);
+    for (int i = 0; i < n * n; ++i) B[i] = A[i];
+    for (int i = 0; i < n; ++i) B[i * n + i] += delta;
+    return chol(n, B, L);
+}
+static void symmetrize(int n, double *A) {
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            const double s = 0.5 * (A[i * n + j] + A[j * n + i]);
+            A[i * n + j] = A[j * n + i] = s;
+        }
+}
+
+// Eqs. pkf_init1/2/3 (and the constants of the innovation log-likelihood)
+// evaluated once in FP64.
+static kf_status_t precompute(const kf_model_t *md, HostModel *h) {
+    const int n = md->nx, m = md->ny;
+    const double *F = md->F, *Q = md->Q, *H = md->H, *R = md->R, *m0 = md->m0, *P0 = md->P0;
+    memset(h, 0, sizeof(*h));
+    h->n = n;
+    h->m = m;
+    double Ht[KF_MAXN * KF_MAXM], Ft[KF_MAXN * KF_MAXN], t1[KF_MAXN * KF_MAXN], t2[KF_MAXN * KF_MAXN];
+    double S[KF_MAXM * KF_MAXM], QHt[KF_MAXN * KF_MAXM], I[KF_MAXN * KF_MAXN];
+    tr(m, n, H, Ht);
+    tr(n, n, F, Ft);
+    for (int i = 0; i < n * n; ++i) I[i] = (i / n == i % n) ? 1.0 : 0.0;
+    // S = H Q H^T + R, K = Q H^T S^{-1}
+    mm(n, n, m, Q, Ht, QHt);
+    mm(m, n, m, H, QHt, t1);
+    for (int i = 0; i < m * m; ++i) S[i] = t1[i] + R[i];
+    symmetrize(m, S);
+    double logdetS;
+    if (!spd_inv(m, S, h->Sinv, &logdetS)) return KF_ERR_NOT_PD;
+    mm(n, m, m, QHt, h->Sinv, h->K);
+    // A = (I - K H) F, C = (I - K H) Q
+    double IKH[KF_MAXN * KF_MAXN];
+    mm(n, m, n, h->K, H, t1);
+    for (int i = 0; i < n * n; ++i) IKH[i] = I[i] - t1[i];
+    mm(n, n, n, IKH, F, h->A);
+    mm(n, n, n, IKH, Q, h->C);
+    symmetrize(n, h->C);
+    // G = F^T H^T S^{-1}, J = G H F
+    double FtHt[KF_MAXN * KF_MAXM];
+    mm(n, n, m, Ft, Ht, FtHt);
+    mm(n, m, m, FtHt, h->Sinv, h->G);
+    mm(m, n, n, H, F, h->HF);
+    mm(n, m, n, h->G, h->HF, h->J);
+    symmetrize(n, h->J);
+    // k = 1: xbar_{1|0} = F m0, P_{1|0} = F P0 F^T + Q, S_1, K_1, b_1 = c1 + K_1 y_1, C_1
+    double x1[KF_MAXN], P1[KF_MAXN * KF_MAXN], S1[KF_MAXM * KF_MAXM], P1Ht[KF_MAXN * KF_MAXM];
+    mm(n, n, 1, F, m0, x1);
+    mm(n, n, n, F, P0, t1);
+    mm(n, n, n, t1, Ft, t2);
+    for (int i = 0; i < n * n; ++i) P1[i] = t2[i] + Q[i];
+    symmetrize(n, P1);
+    mm(n, n, m, P1, Ht, P1Ht);
+    mm(m, n, m, H, P1Ht, t1);
+    for (int i = 0; i < m * m; ++i) S1[i] = t1[i] + R[i];
+    symmetrize(m, S1);
+    double logdetS1;
+    if (!spd_inv(m, S1, h->S1inv, &logdetS1)) return KF_ERR_NOT_PD;
+    mm(n, m, m, P1Ht, h->S1inv, h->K1);
+    mm(m, n, 1, H, x1, h->Hx1);
+    double KHx[KF_MAXN];
+    mm(n, m, 1, h->K1, h->Hx1, KHx);
+    for (int i = 0; i < n; ++i) h->c1[i] = x1[i] - KHx[i];
+    // C_1 = P_{1|0} - K_1 S_1 K_1^T = P_{1|0} - K_1 H P_{1|0}
+    double KH[KF_MAXN * KF_MAXN];
+    mm(n, m, n, h->K1, H, KH);
+    mm(n, n, n, KH, P1, t1);
+    for (int i = 0; i < n * n; ++i) h->C1[i] = P1[i] - t1[i];
+    symmetrize(n, h->C1);
+    const double LOG2PI = 1.8378770664093454835606594728112;
+    h->llc = logdetS + m * LOG2PI;
+    h->llc1 = logdetS1 + m * LOG2PI;
+    for (int i = 0; i < n * n; ++i) {
+        h->F[i] = F[i];
+        h->Q[i] = Q[i];
+    }
+    symmetrize(n, h->Q);
+    return KF_OK;
+}
+
+// ---------------------------------------------------------------- process state
+
+static std::mutex g_mu;
+static void *g_ws[64];
+static size_t g_ws_bytes[64];
+static int *g_status[64];
+static std::atomic<int64_t> g_opt[8] = {1000000000LL, -1, 0, 0, 0, 0, 0, 0};
+
+static kf_status_t from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return KF_OK;
+    if (e == cudaErrorMemoryAllocation) return KF_ERR_OOM;
+    return KF_ERR_CUDA;
+}
+
+static kf_status_t device_status_word(int **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (dev < 0 || dev >= 64) return KF_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_status[dev]) {
+        int *p = nullptr;
+        e = cudaMalloc(&p, sizeof(int));
+        if (e != cudaSuccess) return from_cuda(e);
+        e = cudaMemset(p, 0, sizeof(int));
+        if (e != cudaSuccess) return from_cuda(e);
+        g_status[dev] = p;
+    }
+    *out = g_status[dev];
+    return KF_OK;
+}
+
+static kf_status_t library_workspace(size_t bytes, void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (dev < 0 || dev >= 64) return KF_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_ws_bytes[dev] < bytes) {
+        if (g_ws[dev]) {
+            cudaDeviceSynchronize();   // the old buffer may still be in use
+            cudaFree(g_ws[dev]);
+            g_ws[dev] = nullptr;
+            g_ws_bytes[dev] = 0;
+        }
+        size_t want = bytes + bytes / 4;
+        e = cudaMalloc(&g_ws[dev], want);
+        if (e != cudaSuccess) {
+            g_ws[dev] = nullptr;
+            return from_cuda(e);
+        }
+        g_ws_bytes[dev] = want;
+    }
+    *out = g_ws[dev];
+    return KF_OK;
+}
+
+static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static kf_status_t check_model(const kf_model_t *md) {
+    if (!md) return KF_ERR_ARG;
+    if (md->nx != 2 && md->nx != 4 && md->nx != 8) return KF_ERR_ARG;
+    if (md->ny < 1 || md->ny > KF_MAXM) return KF_ERR_ARG;
+    if (!md->F || !md->Q || !md->H || !md->R || !md->m0 || !md->P0) return KF_ERR_ARG;
+    const int n = md->nx, m = md->ny;
+    for (int i = 0; i < n * n; ++i)
+        if (!isfinite(md->F[i])) return KF_ERR_ARG;
+    for (int i = 0; i < m * n; ++i)
+        if (!isfinite(md->H[i])) return KF_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!isfinite(md->m0[i])) return KF_ERR_ARG;
+    double L[KF_MAXM * KF_MAXM];
+    if (!is_symmetric(m, md->R) || !chol(m, md->R, L)) return KF_ERR_NOT_PD;
+    if (!is_spsd(n, md->Q) || !is_spsd(n, md->P0)) return KF_ERR_NOT_PD;
+    return KF_OK;
+}
+
+static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, kf_precision_t prec,
+                       kf_scan_t scan, void *m1, void *P1, void *m2, void *P2, double *loglik, void *workspace,
+                       void *stream) {
+    kf_status_t s = check_model(md);
+    if (s != KF_OK) return s;
+    if (T < 1 || T > (int64_t(1) << 40) || !y) return KF_ERR_ARG;
+    if (prec != KF_FP64 && prec != KF_FP32 && prec != KF_FP32_FP64SOLVE) return KF_ERR_ARG;
+    if (scan < KF_SCAN_AUTO || scan > KF_SCAN_LADNER_FISCHER) return KF_ERR_ARG;
+    const size_t w = (prec == KF_FP64) ? 8 : 4;
+    LaunchReq q;
+    memset(&q, 0, sizeof(q));
+    q.op = op;
+    q.prec = int(prec);
+    q.scan = (scan == KF_SCAN_AUTO) ? KF_SCAN_DLB_I : int(scan);
+    q.T = T;
+    q.y = y;
+    if (op == KF_OP_FILTER_I) {
+        if (!m1) return KF_ERR_ARG;
+        q.mf_user = m1;
+        q.Pf_user = P1;
+    } else {
+        if (!m1 || !P1) return KF_ERR_ARG;
+        q.ms = m1;
+        q.Ps = P1;
+        q.mf_user = m2;
+        q.Pf_user = P2;
+    }
+    const void *ptrs[] = {y, m1, P1, m2, P2};
+    for (const void *p : ptrs)
+        if (p && !aligned(p, w)) return KF_ERR_ARG;
+    if (loglik && !aligned(loglik, 8)) return KF_ERR_ARG;
+    if (workspace && !aligned(workspace, 256)) return KF_ERR_ARG;
+    HostModel hm;
+    s = precompute(md, &hm);
+    if (s != KF_OK) return s;
+    q.hm = &hm;
+    q.loglik = loglik;
+    q.stream = static_cast<cudaStream_t>(stream);
+    q.timeout_ns = g_opt[KF_OPT_WAIT_TIMEOUT_NS].load();
+    q.inject_skip_tile = int(g_opt[KF_OPT_TEST_SKIP_TILE].load());
+    q.k_override = int(g_opt[KF_OPT_POSITIONS_PER_THREAD].load());
+    q.threads = int(g_opt[KF_OPT_THREADS].load());
+    s = device_status_word(&q.status);
+    if (s != KF_OK) return s;
+    const size_t need = ws_bytes_dispatch(md->nx, op, q.prec, q.scan, T);
+    if (workspace) {
+        q.ws = workspace;
+    } else {
+        s = library_workspace(need, &q.ws);
+        if (s != KF_OK) return s;
+    }
+    return from_cuda(launch_dispatch(q));
+}
+
+}  // namespace kfs
+
+using namespace kfs;
+
+extern "C" {
+
+const char *kf_status_string(kf_status_t s) {
+    switch (s) {
+        case KF_OK: return "ok";
+        case KF_ERR_ARG: return "invalid argument";
+        case KF_ERR_NOT_PD: return "covariance not positive (semi-)definite";
+        case KF_ERR_CUDA: return "CUDA error";
+        case KF_ERR_OOM: return "out of device memory";
+        case KF_ERR_TIMEOUT: return "bounded wait timed out in a kernel";
+        case KF_ERR_BUDGET: return "job exceeds the device memory budget";
+        case KF_ERR_BUSY: return "queue full or unknown job";
+    }
+    return "unknown status";
+}
+
+const char *kf_version(void) { return "kfscan 0.1 (sm_103a)"; }
+
+size_t kf_workspace_size(kf_op_t op, int nx, int ny, int64_t total_steps, kf_precision_t prec, kf_scan_t scan) {
+    if ((nx != 2 && nx != 4 && nx != 8) || ny < 1 || ny > KF_MAXM || total_steps < 1) return 0;
+    if (op < KF_OP_FILTER || op > KF_OP_TWO_FILTER) return 0;
+    if (prec != KF_FP64 && prec != KF_FP32 && prec != KF_FP32_FP64SOLVE) return 0;
+    if (scan < KF_SCAN_AUTO || scan > KF_SCAN_LADNER_FISCHER) return 0;
+    const int sc = (scan == KF_SCAN_AUTO) ? KF_SCAN_DLB_I : int(scan);
+    return ws_bytes_dispatch(nx, int(op), int(prec), sc, total_steps);
+}
+
+kf_status_t kf_filter(const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec, kf_scan_t scan,
+                      void *m_out, void *P_out, double *loglik, void *workspace, void *stream) {
+    return run(KF_OP_FILTER_I, model, T, y, prec, scan, m_out, P_out, nullptr, nullptr, loglik, workspace, stream);
+}
+
+kf_status_t kf_rts_smooth(const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec, kf_scan_t scan,
+                          void *ms_out, void *Ps_out, void *mf_out, void *Pf_out, double *loglik, void *workspace,
+                          void *stream) {
+    return run(KF_OP_RTS_I, model, T, y, prec, scan, ms_out, Ps_out, mf_out, Pf_out, loglik, workspace, stream);
+}
+
+kf_status_t kf_two_filter_smooth(const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec,
+                                 kf_scan_t scan, void *ms_out, void *Ps_out, void *mf_out, void *Pf_out,
+                                 double *loglik, void *workspace, void *stream) {
+    return run(KF_OP_TF_I, model, T, y, prec, scan, ms_out, Ps_out, mf_out, Pf_out, loglik, workspace, stream);
+}
+
+kf_status_t kf_sync_status(void *stream) {
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return KF_ERR_CUDA;
+    int *p = nullptr;
+    kf_status_t s = device_status_word(&p);
+    if (s != KF_OK) return s;
+    int v = 0;
+    e = cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return KF_ERR_CUDA;
+    if (v != 0) {
+        e = cudaMemset(p, 0, sizeof(int));
+        if (e != cudaSuccess) return KF_ERR_CUDA;
+        return kf_status_t(v);
+    }
+    return KF_OK;
+}
+
+kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_THREADS) return KF_ERR_ARG;
+    if (opt == KF_OPT_WAIT_TIMEOUT_NS && (value < 1000000 || value > 60000000000LL)) return KF_ERR_ARG;
+    if (opt == KF_OPT_POSITIONS_PER_THREAD && (value < 0 || value > (1 << 24))) return KF_ERR_ARG;
+    if (opt == KF_OPT_THREADS && value != 0 && value != 128) return KF_ERR_ARG;
+    g_opt[opt].store(value);
+    return KF_OK;
+}
+
+int64_t kf_get_option(kf_option_t opt) {
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_THREADS) return -1;
+    return g_opt[opt].load();
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// kf_host.h -- declarations shared by the C-ABI layer (kf_api.cu) and the
+// per-state-dimension launch units (kf_n2.cu, kf_n4.cu, kf_n8.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+
+#define KF_MAXN 8
+#define KF_MAXM 8
+#define KF_MAX_TILES 1024
+
+// integer mirrors of the public enums (kfscan.h)
+#define KF_OP_FILTER_I 0
+#define KF_OP_RTS_I 1
+#define KF_OP_TF_I 2
+#define KF_SCAN_DLB_I 1
+#define KF_SCAN_HS_I 2
+#define KF_SCAN_BLELLOCH_I 3
+#define KF_SCAN_LAFI_I 4
+#define KF_FP64_I 0
+#define KF_FP32_I 1
+#define KF_FP32_FP64SOLVE_I 2
+
+namespace kfs {
+
+// k-invariant model quantities in FP64, n x n / n x m / m x m row-major with
+// the runtime sizes n, m (see FiltParams in kf_math.cuh for their meaning).
+struct HostModel {
+    int n, m;
+    double A[KF_MAXN * KF_MAXN], C[KF_MAXN * KF_MAXN], J[KF_MAXN * KF_MAXN];
+    double K[KF_MAXN * KF_MAXM], G[KF_MAXN * KF_MAXM];
+    double K1[KF_MAXN * KF_MAXM], c1[KF_MAXN], C1[KF_MAXN * KF_MAXN];
+    double HF[KF_MAXM * KF_MAXN], Sinv[KF_MAXM * KF_MAXM], S1inv[KF_MAXM * KF_MAXM], Hx1[KF_MAXM];
+    double llc, llc1;
+    double F[KF_MAXN * KF_MAXN], Q[KF_MAXN * KF_MAXN];
+};
+
+struct LaunchReq {
+    int op, prec, scan;
+    int64_t T;
+    const HostModel *hm;
+    const void *y;
+    void *mf_user, *Pf_user, *ms, *Ps;
+    double *loglik;
+    void *ws;
+    cudaStream_t stream;
+    int *status;
+    int64_t timeout_ns;
+    int inject_skip_tile;
+    int k_override;      // positions per thread (0: planner's choice)
+    int threads;         // CTA size of the decoupled look-back scan (0: default)
+};
+
+size_t ws_bytes_dispatch(int nx, int op, int prec, int scan, int64_t T);
+cudaError_t launch_dispatch(const LaunchReq &q);
+
+// per-(N, precision) entry points, one translation unit each (kf_n<N>_<p>.cu)
+#define KF_DECL_UNIT(N, P) \
+    size_t ws_bytes_n##N##_##P(int op, int scan, int64_t T); \
+    cudaError_t launch_n##N##_##P(const LaunchReq &q);
+KF_DECL_UNIT(2, f64) KF_DECL_UNIT(2, f32) KF_DECL_UNIT(2, mix)
+KF_DECL_UNIT(4, f64) KF_DECL_UNIT(4, f32) KF_DECL_UNIT(4, mix)
+KF_DECL_UNIT(8, f64) KF_DECL_UNIT(8, f32) KF_DECL_UNIT(8, mix)
+#undef KF_DECL_UNIT
+
+}  // namespace kfs

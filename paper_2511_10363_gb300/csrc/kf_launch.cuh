@@ -1,0 +1,268 @@
+// kf_launch.cuh -- host-side planning and launch of the scans for one state
+// dimension N.  Included once per N by kf_n{2,4,8}.cu.
+#pragma once
+
+#include "kf_host.h"
+#include "scan_levels.cuh"
+
+namespace kfs {
+
+template <int N, typename R>
+void to_params(const HostModel &h, FiltParams<N, R> &p) {
+    static_assert(N <= KF_MAXN, "N too large");
+    memset(&p, 0, sizeof(p));
+    const int n = N;
+    for (int i = 0; i < n * n; ++i) {
+        p.A[i] = R(h.A[i]);
+        p.F[i] = R(h.F[i]);
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) {
+            p.C[su(N, i, j)] = R(h.C[i * n + j]);
+            p.J[su(N, i, j)] = R(h.J[i * n + j]);
+            p.C1[su(N, i, j)] = R(h.C1[i * n + j]);
+            p.Q[su(N, i, j)] = R(h.Q[i * n + j]);
+        }
+    for (int i = 0; i < n; ++i) {
+        p.c1[i] = R(h.c1[i]);
+        for (int j = 0; j < h.m; ++j) {
+            p.K[i * MAXNY + j] = R(h.K[i * h.m + j]);
+            p.G[i * MAXNY + j] = R(h.G[i * h.m + j]);
+            p.K1[i * MAXNY + j] = R(h.K1[i * h.m + j]);
+        }
+    }
+    for (int j = 0; j < h.m; ++j) {
+        p.Hx1[j] = R(h.Hx1[j]);
+        for (int k = 0; k < n; ++k) p.HF[j * N + k] = R(h.HF[j * n + k]);
+        for (int k = 0; k < h.m; ++k) {
+            p.Sinv[j * MAXNY + k] = R(h.Sinv[j * h.m + k]);
+            p.S1inv[j * MAXNY + k] = R(h.S1inv[j * h.m + k]);
+        }
+    }
+    p.llc = h.llc;
+    p.llc1 = h.llc1;
+    p.ny = h.m;
+}
+
+// ---------------------------------------------------------------- tile plan
+
+template <class P, int THREADS, int V>
+static int max_resident_tiles(int device) {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dlb_scan_kernel<P, THREADS, V>, THREADS, 0);
+    if (per_sm < 1) per_sm = 1;
+    return sms * per_sm;
+}
+
+struct TilePlan {
+    int ntiles, K;
+};
+
+// One wave of resident CTAs (never more tiles than the look-back window),
+// unless the request fixes the positions per thread.
+static TilePlan plan_tiles(int64_t total, int threads, int window, int resident, int k_override) {
+    TilePlan t;
+    int64_t G = resident < window ? resident : window;
+    int64_t per = (total + G * threads - 1) / (G * threads);
+    if (per < 1) per = 1;
+    if (k_override > 0) per = k_override;
+    int64_t g = (total + per * threads - 1) / (per * threads);
+    while (g > window) {   // a fixed K that would need more tiles than the window
+        ++per;
+        g = (total + per * threads - 1) / (per * threads);
+    }
+    t.K = int(per);
+    t.ntiles = int(g < 1 ? 1 : g);
+    return t;
+}
+
+// ---------------------------------------------------------------- workspace layout
+
+// Regions, each 256-byte aligned:
+//   ctl_f  : counters[2] + flags[KF_MAX_TILES]   (forward scan)
+//   ctl_r  : counters[2] + flags[KF_MAX_TILES]   (reverse scan)
+//   agg    : KF_MAX_TILES * max element size * sizeof(R)
+//   incl   : KF_MAX_TILES * max carry size * sizeof(R)
+//   llpart : KF_MAX_TILES doubles
+//   mf, Pf : filter means [T][N] and packed covariances [T][S] (smoothers)
+//   lv_a, lv_b : level-scan element buffers [ES][Tpad] (level algorithms)
+struct WsLayout {
+    size_t ctl_f, ctl_r, agg, incl, llpart, mf, Pf, lv_a, lv_b, total;
+};
+
+static inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static inline int64_t next_pow2(int64_t t) {
+    int64_t p = 1;
+    while (p < t) p <<= 1;
+    return p;
+}
+
+template <int N, typename R>
+WsLayout ws_layout(int op, int scan, int64_t T) {
+    constexpr int S = N * (N + 1) / 2;
+    constexpr int ES = FElem<N, R>::SIZE;  // >= RElem size
+    constexpr int CS = FwdCarry<N, R>::SIZE;
+    WsLayout L;
+    size_t o = 0;
+    const size_t ctl = al256(sizeof(int) * (2 + KF_MAX_TILES));
+    L.ctl_f = o; o += ctl;
+    L.ctl_r = o; o += ctl;
+    L.agg = o; o += al256(size_t(KF_MAX_TILES) * ES * sizeof(R));
+    L.incl = o; o += al256(size_t(KF_MAX_TILES) * CS * sizeof(R));
+    L.llpart = o; o += al256(size_t(KF_MAX_TILES) * sizeof(double));
+    L.mf = L.Pf = L.lv_a = L.lv_b = 0;
+    if (op != KF_OP_FILTER_I) {
+        L.mf = o; o += al256(size_t(T) * N * sizeof(R));
+        L.Pf = o; o += al256(size_t(T) * S * sizeof(R));
+    }
+    if (scan != KF_SCAN_DLB_I) {
+        const int64_t Tp = next_pow2(T);
+        L.lv_a = o; o += al256(size_t(Tp) * ES * sizeof(R));
+        if (scan == KF_SCAN_HS_I || scan == KF_SCAN_BLELLOCH_I) { L.lv_b = o; o += al256(size_t(Tp) * ES * sizeof(R)); }
+    }
+    L.total = o;
+    return L;
+}
+
+// ---------------------------------------------------------------- one scan
+
+template <class P, int THREADS, int V>
+static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_off, const WsLayout &L,
+                           const LaunchReq &q, double *ll_out) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int64_t total = P::total(args);
+    const TilePlan tp = plan_tiles(total, THREADS, THREADS * V, max_resident_tiles<P, THREADS, V>(dev), q.k_override);
+    DlbCtl ctl;
+    ctl.counters = reinterpret_cast<int *>(ws + ctl_off);
+    ctl.flags = ctl.counters + 2;
+    ctl.agg = ws + L.agg;
+    ctl.incl = ws + L.incl;
+    ctl.ll_part = reinterpret_cast<double *>(ws + L.llpart);
+    ctl.ll_out = ll_out;
+    ctl.status = q.status;
+    ctl.timeout_ns = q.timeout_ns;
+    ctl.ntiles = tp.ntiles;
+    ctl.K = tp.K;
+    ctl.inject_skip_tile = q.inject_skip_tile;
+    cudaError_t e = cudaMemsetAsync(ctl.counters, 0, sizeof(int) * (2 + tp.ntiles), q.stream);
+    if (e != cudaSuccess) return e;
+    dlb_scan_kernel<P, THREADS, V><<<tp.ntiles, THREADS, 0, q.stream>>>(args, ctl);
+    return cudaGetLastError();
+}
+
+static inline int lv_grid(int64_t work, int threads) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t g = (work + threads - 1) / threads;
+    const int64_t cap = int64_t(sms) * 8;
+    if (g > cap) g = cap;
+    return int(g < 1 ? 1 : g);
+}
+
+template <class P>
+static cudaError_t run_levels(const typename P::Args &args, char *ws, size_t ctl_off, const WsLayout &L,
+                              const LaunchReq &q, double *ll_out) {
+    using R = typename P::R;
+    constexpr int LT = 128;
+    const int64_t total = P::total(args);
+    const int64_t Tp = next_pow2(total);
+    int Lg = 0;
+    while ((int64_t(1) << Lg) < Tp) ++Lg;
+    R *a = reinterpret_cast<R *>(ws + L.lv_a);
+    R *b = L.lv_b ? reinterpret_cast<R *>(ws + L.lv_b) : nullptr;
+    cudaStream_t st = q.stream;
+    R *res = a;
+    if (q.scan == KF_SCAN_HS_I) {
+        lv_build<P><<<lv_grid(Tp, LT), LT, 0, st>>>(args, a, nullptr, Tp);
+        R *src = a, *dst = b;
+        for (int d = 0; d < Lg; ++d) {
+            lv_hillis_steele<P><<<lv_grid(Tp, LT), LT, 0, st>>>(src, dst, Tp, int64_t(1) << d);
+            R *t = src; src = dst; dst = t;
+        }
+        res = src;
+    } else if (q.scan == KF_SCAN_BLELLOCH_I) {
+        lv_build<P><<<lv_grid(Tp, LT), LT, 0, st>>>(args, a, b, Tp);
+        for (int d = 0; d < Lg; ++d) lv_upsweep<P><<<lv_grid(Tp >> (d + 1), LT), LT, 0, st>>>(a, Tp, d);
+        lv_set_identity<P><<<1, 32, 0, st>>>(a, Tp, Tp - 1);
+        for (int d = Lg - 1; d >= 0; --d) lv_blelloch_down<P><<<lv_grid(Tp >> (d + 1), LT), LT, 0, st>>>(a, Tp, d);
+        lv_blelloch_final<P><<<lv_grid(Tp, LT), LT, 0, st>>>(a, b, Tp);
+    } else {  // Ladner-Fischer
+        lv_build<P><<<lv_grid(Tp, LT), LT, 0, st>>>(args, a, nullptr, Tp);
+        for (int d = 0; d < Lg; ++d) lv_upsweep<P><<<lv_grid(Tp >> (d + 1), LT), LT, 0, st>>>(a, Tp, d);
+        for (int d = Lg - 1; d >= 0; --d) {
+            const int64_t n = (Tp >> (d + 1)) - 1;
+            if (n > 0) lv_lafi_down<P><<<lv_grid(n, LT), LT, 0, st>>>(a, Tp, d);
+        }
+    }
+    int *counter = reinterpret_cast<int *>(ws + ctl_off);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int) * 2, st);
+    if (e != cudaSuccess) return e;
+    int g = lv_grid(total, LT);
+    if (g > KF_MAX_TILES) g = KF_MAX_TILES;
+    lv_extract<P, LT><<<g, LT, 0, st>>>(args, res, Tp, reinterpret_cast<double *>(ws + L.llpart), counter, ll_out);
+    return cudaGetLastError();
+}
+
+template <class P, int THREADS, int V>
+static cudaError_t run_scan(const typename P::Args &args, char *ws, size_t ctl_off, const WsLayout &L,
+                            const LaunchReq &q, double *ll_out) {
+    if (q.scan == KF_SCAN_DLB_I) return run_dlb<P, THREADS, V>(args, ws, ctl_off, L, q, ll_out);
+    return run_levels<P>(args, ws, ctl_off, L, q, ll_out);
+}
+
+// ---------------------------------------------------------------- one operation
+
+template <int N, typename R, int MODE, int THREADS>
+static cudaError_t launch_typed(const LaunchReq &q) {
+    using Src = OneSeq<N, R>;
+    constexpr int V = (1024 + THREADS - 1) / THREADS;
+    static_assert(THREADS * V <= KF_MAX_TILES, "look-back window larger than the flag array");
+    const WsLayout L = ws_layout<N, R>(q.op, q.scan, q.T);
+    char *ws = static_cast<char *>(q.ws);
+    KfBufs<R> buf;
+    buf.y = static_cast<const R *>(q.y);
+    buf.ms = static_cast<R *>(q.ms);
+    buf.Ps = static_cast<R *>(q.Ps);
+    if (q.op == KF_OP_FILTER_I) {
+        buf.mf = nullptr;
+        buf.Pf = nullptr;
+    } else {
+        buf.mf = reinterpret_cast<R *>(ws + L.mf);
+        buf.Pf = reinterpret_cast<R *>(ws + L.Pf);
+    }
+    buf.mf_user = static_cast<R *>(q.mf_user);
+    buf.Pf_user = static_cast<R *>(q.Pf_user);
+
+    typename FilterFwd<N, R, MODE, Src>::Args fa;
+    to_params<N, R>(*q.hm, fa.src.prm);
+    fa.src.T = q.T;
+    fa.buf = buf;
+    fa.want_ll = q.loglik != nullptr;
+    cudaError_t e = run_scan<FilterFwd<N, R, MODE, Src>, THREADS, V>(fa, ws, L.ctl_f, L, q, q.loglik);
+    if (e != cudaSuccess || q.op == KF_OP_FILTER_I) return e;
+    if (q.op == KF_OP_RTS_I) {
+        typename RtsRev<N, R, Src>::Args ra;
+        ra.src = fa.src;
+        ra.buf = buf;
+        ra.want_ll = 0;
+        return run_scan<RtsRev<N, R, Src>, THREADS, V>(ra, ws, L.ctl_r, L, q, nullptr);
+    }
+    typename TfRev<N, R, MODE, Src>::Args ta;
+    ta.src = fa.src;
+    ta.buf = buf;
+    ta.want_ll = 0;
+    return run_scan<TfRev<N, R, MODE, Src>, THREADS, V>(ta, ws, L.ctl_r, L, q, nullptr);
+}
+
+template <int N>
+size_t ws_bytes_n(int op, int prec, int scan, int64_t T) {
+    if (prec == KF_FP64_I) return ws_layout<N, double>(op, scan, T).total;
+    return ws_layout<N, float>(op, scan, T).total;
+}
+
+
+}  // namespace kfs

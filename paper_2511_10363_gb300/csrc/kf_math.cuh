@@ -1,0 +1,775 @@
+// kf_math.cuh -- register-resident small-matrix blocks and the associative
+// operators of arXiv 2511.10363 (Sec. IV-C Lemma 1, Sec. IV-D Lemma 2), the
+// element constructions (Eqs. pkf_init1/2/3, prts_init1/2) and the
+// two-filter merge (Eqs. mean_tf_combination / cov_tf_combination).
+//
+// Every block is a fixed-size array indexed only with compile-time indices
+// after unrolling, so it lives in registers.  Symmetric matrices (C, J, L,
+// covariances) are stored as their packed upper triangle, which makes every
+// produced covariance exactly symmetric.
+//
+// One-sided forms.  In Lemma 1 the outputs b_ij and C_ij depend on the left
+// operand only through (b_i, C_i), and eta_ij, J_ij depend on the right
+// operand only through (eta_j, J_j).  In Lemma 2, g_ij and L_ij depend on the
+// right operand only through (g_j, L_j).  A scan carry therefore holds only
+// the half it is extracted from, and applying an element to it evaluates
+// only that half of the operator ("apply_*" below).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#define KF_HD __host__ __device__ __forceinline__
+#define KF_D __device__ __forceinline__
+
+namespace kfs {
+
+constexpr int MAXNY = 8;
+
+// packed upper-triangular index, row-major over i <= j
+KF_HD constexpr int su(int N, int i, int j) { return i * N - (i * (i - 1)) / 2 + (j - i); }
+KF_HD constexpr int si(int N, int i, int j) { return i <= j ? su(N, i, j) : su(N, j, i); }
+
+// ---------------------------------------------------------------- elements
+
+// Filtering element (A, b, C, eta, J) of Sec. IV-C; C and J packed symmetric.
+template <int N, typename R>
+struct FElem {
+    static constexpr int NN = N * N, S = N * (N + 1) / 2;
+    static constexpr int oA = 0, ob = NN, oC = NN + N, oe = NN + N + S, oJ = NN + 2 * N + S;
+    static constexpr int SIZE = NN + 2 * N + 2 * S;
+    R v[SIZE];
+};
+
+// Forward filtering carry: (b, C) of a prefix a_1 (x) ... (x) a_k.
+template <int N, typename R>
+struct FwdCarry {
+    static constexpr int S = N * (N + 1) / 2, ob = 0, oC = N, SIZE = N + S;
+    R v[SIZE];
+};
+
+// Backward information carry: (eta, J) of a suffix a_{k+1} (x) ... (x) e.
+template <int N, typename R>
+struct RevCarry {
+    static constexpr int S = N * (N + 1) / 2, oe = 0, oJ = N, SIZE = N + S;
+    R v[SIZE];
+};
+
+// RTS element (E, g, L) of Sec. IV-D; L packed symmetric.
+template <int N, typename R>
+struct RElem {
+    static constexpr int NN = N * N, S = N * (N + 1) / 2;
+    static constexpr int oE = 0, og = NN, oL = NN + N, SIZE = NN + N + S;
+    R v[SIZE];
+};
+
+// RTS carry: (g, L) of a suffix a_k (x) ... (x) a_T.
+template <int N, typename R>
+struct RCarry {
+    static constexpr int S = N * (N + 1) / 2, og = 0, oL = N, SIZE = N + S;
+    R v[SIZE];
+};
+
+template <class X>
+KF_HD void set_zero(X &x) {
+#pragma unroll
+    for (int i = 0; i < X::SIZE; ++i) x.v[i] = 0;
+}
+
+// (I, 0, 0, 0, 0): the neutral element of Lemma 1.
+template <int N, typename R>
+KF_HD void set_identity(FElem<N, R> &e) {
+    set_zero(e);
+#pragma unroll
+    for (int i = 0; i < N; ++i) e.v[FElem<N, R>::oA + i * N + i] = R(1);
+}
+
+// (I, 0, 0): the neutral element of Lemma 2.
+template <int N, typename R>
+KF_HD void set_identity(RElem<N, R> &e) {
+    set_zero(e);
+#pragma unroll
+    for (int i = 0; i < N; ++i) e.v[RElem<N, R>::oE + i * N + i] = R(1);
+}
+
+// ---------------------------------------------------------------- model constants
+
+// k-invariant quantities, computed on the host in FP64 and rounded once to
+// the working precision R.
+template <int N, typename R>
+struct FiltParams {
+    static constexpr int NN = N * N, S = N * (N + 1) / 2;
+    R A[NN], C[S], J[S];          // a_k, k >= 2: Eq. pkf_init1 and Eq. pkf_init3
+    R K[N * MAXNY];               // b_k = K y_k              (K = Q H^T S^{-1})
+    R G[N * MAXNY];               // eta_k = G y_k            (G = F^T H^T S^{-1})
+    R K1[N * MAXNY], c1[N], C1[S];// a_1, Eq. pkf_init2: b_1 = c1 + K1 y_1
+    R HF[MAXNY * N];              // log-likelihood: v_k = y_k - H F xbar_{k-1|k-1}
+    R Sinv[MAXNY * MAXNY];        //   S^{-1}, S = H Q H^T + R
+    R S1inv[MAXNY * MAXNY];       //   S_1^{-1}, S_1 = H P_{1|0} H^T + R
+    R Hx1[MAXNY];                 //   H xbar_{1|0}
+    double llc, llc1;             //   log det S + m log 2 pi,  log det S_1 + m log 2 pi
+    R F[NN], Q[S];                // RTS elements, Eq. prts_init1
+    int ny;
+};
+
+// ---------------------------------------------------------------- small solves
+
+// X = (I + C J)^{-1} for packed symmetric C, J, by Gauss-Jordan elimination
+// with partial pivoting in precision T.  Returns sum log|pivot| = log det(I + C J)
+// in `logdet` when LD (det(I + C J) >= 1 for positive semi-definite C, J).
+template <int N, typename T, bool LD, typename RC, typename RJ>
+KF_D void inv_I_plus_CJ_T(const RC *C, const RJ *J, T X[N * N], T &logdet) {
+    T a[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            T s = (r == c) ? T(1) : T(0);
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += T(C[si(N, r, k)]) * T(J[si(N, k, c)]);
+            a[r * N + c] = s;
+            X[r * N + c] = (r == c) ? T(1) : T(0);
+        }
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        int p = c;
+        T best = fabs(a[c * N + c]);
+#pragma unroll
+        for (int r = c + 1; r < N; ++r) {
+            T v = fabs(a[r * N + c]);
+            if (v > best) { best = v; p = r; }
+        }
+#pragma unroll
+        for (int r = c + 1; r < N; ++r) {
+            const bool s = (p == r);
+#pragma unroll
+            for (int j = c; j < N; ++j) {
+                T u = a[c * N + j], w = a[r * N + j];
+                a[c * N + j] = s ? w : u;
+                a[r * N + j] = s ? u : w;
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                T u = X[c * N + j], w = X[r * N + j];
+                X[c * N + j] = s ? w : u;
+                X[r * N + j] = s ? u : w;
+            }
+        }
+        const T piv = a[c * N + c];
+        if (LD) logdet += log(fabs(piv));
+        const T d = T(1) / piv;
+#pragma unroll
+        for (int j = c + 1; j < N; ++j) a[c * N + j] *= d;
+#pragma unroll
+        for (int j = 0; j < N; ++j) X[c * N + j] *= d;
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            if (r == c) continue;
+            const T f = a[r * N + c];
+#pragma unroll
+            for (int j = c + 1; j < N; ++j) a[r * N + j] -= f * a[c * N + j];
+#pragma unroll
+            for (int j = 0; j < N; ++j) X[r * N + j] -= f * X[c * N + j];
+        }
+    }
+}
+
+// Solve-precision policy.  MODE 0: everything in R.  MODE 1 (R = float):
+// Gauss-Jordan in FP32, then one step of iterative refinement with the
+// residual E = I - M X formed in FP64 from M = I + C J built in FP64, and
+// the correction X <- X + X E applied in FP32; log det in FP64.
+template <int N, typename R, int MODE, bool LD>
+KF_D void inv_I_plus_CJ(const R *C, const R *J, R X[N * N], double &logdet) {
+    if constexpr (MODE == 0) {
+        R ld = 0;
+        inv_I_plus_CJ_T<N, R, LD>(C, J, X, ld);
+        if (LD) logdet += double(ld);
+    } else {
+        static_assert(sizeof(R) == 4, "the refined solve is for FP32 elements");
+        R ld = 0;
+        inv_I_plus_CJ_T<N, R, false>(C, J, X, ld);
+        double Md[N * N];
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                double s = (r == c) ? 1.0 : 0.0;
+#pragma unroll
+                for (int k = 0; k < N; ++k) s += double(C[si(N, r, k)]) * double(J[si(N, k, c)]);
+                Md[r * N + c] = s;
+            }
+        R E[N * N];
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                double s = (r == c) ? 1.0 : 0.0;
+#pragma unroll
+                for (int k = 0; k < N; ++k) s -= Md[r * N + k] * double(X[k * N + c]);
+                E[r * N + c] = R(s);
+            }
+        R Xn[N * N];
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                R s = X[r * N + c];
+#pragma unroll
+                for (int k = 0; k < N; ++k) s += X[r * N + k] * E[k * N + c];
+                Xn[r * N + c] = s;
+            }
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) X[i] = Xn[i];
+        if constexpr (LD) {
+            // log det M by an FP64 LU of M without refinement: M is only N x N
+            double a[N * N];
+#pragma unroll
+            for (int i = 0; i < N * N; ++i) a[i] = Md[i];
+            double l = 0;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                int p = c;
+                double best = fabs(a[c * N + c]);
+#pragma unroll
+                for (int r = c + 1; r < N; ++r) {
+                    double v = fabs(a[r * N + c]);
+                    if (v > best) { best = v; p = r; }
+                }
+#pragma unroll
+                for (int r = c + 1; r < N; ++r) {
+                    const bool s = (p == r);
+#pragma unroll
+                    for (int j = c; j < N; ++j) {
+                        double u = a[c * N + j], w = a[r * N + j];
+                        a[c * N + j] = s ? w : u;
+                        a[r * N + j] = s ? u : w;
+                    }
+                }
+                const double piv = a[c * N + c];
+                l += log(fabs(piv));
+                const double d = 1.0 / piv;
+#pragma unroll
+                for (int r = c + 1; r < N; ++r) {
+                    const double f = a[r * N + c] * d;
+#pragma unroll
+                    for (int j = c + 1; j < N; ++j) a[r * N + j] -= f * a[c * N + j];
+                }
+            }
+            logdet += l;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Lemma 1
+
+// Full operator of Lemma 1: o = ei (x) ej (ei earlier in time).
+//   X = (I + C_i J_j)^{-1},  Z = X A_i
+//   A_ij = A_j Z
+//   b_ij = A_j X (b_i + C_i eta_j) + b_j
+//   C_ij = A_j D A_j^T + C_j,  D = X C_i (symmetric)
+//   eta_ij = Z^T (eta_j - J_j b_i) + eta_i         [A_i^T (I + J_j C_i)^{-1} = Z^T]
+//   J_ij = Z^T (J_j A_i) + J_i
+template <int N, typename R, int MODE>
+KF_D void lemma1(const FElem<N, R> &ei, const FElem<N, R> &ej, FElem<N, R> &o) {
+    using E = FElem<N, R>;
+    const R *Ai = ei.v + E::oA, *bi = ei.v + E::ob, *Ci = ei.v + E::oC, *ei_ = ei.v + E::oe, *Ji = ei.v + E::oJ;
+    const R *Aj = ej.v + E::oA, *bj = ej.v + E::ob, *Cj = ej.v + E::oC, *ej_ = ej.v + E::oe, *Jj = ej.v + E::oJ;
+    R X[N * N];
+    double ld = 0;
+    inv_I_plus_CJ<N, R, MODE, false>(Ci, Jj, X, ld);
+    R Z[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += X[r * N + k] * Ai[k * N + c];
+            Z[r * N + c] = s;
+        }
+    // b
+    R t[N], u[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = bi[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += Ci[si(N, r, k)] * ej_[k];
+        t[r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += X[r * N + k] * t[k];
+        u[r] = s;
+    }
+    // D = X C_i (upper), AD = A_j D
+    R D[N * (N + 1) / 2];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = r; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += X[r * N + k] * Ci[si(N, k, c)];
+            D[su(N, r, c)] = s;
+        }
+    R AD[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Aj[r * N + k] * D[si(N, k, c)];
+            AD[r * N + c] = s;
+        }
+    // eta: w = eta_j - J_j b_i
+    R w[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = ej_[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s -= Jj[si(N, r, k)] * bi[k];
+        w[r] = s;
+    }
+    // W = J_j A_i
+    R W[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Jj[si(N, r, k)] * Ai[k * N + c];
+            W[r * N + c] = s;
+        }
+    // outputs
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Aj[r * N + k] * Z[k * N + c];
+            o.v[E::oA + r * N + c] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = bj[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += Aj[r * N + k] * u[k];
+        o.v[E::ob + r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = r; c < N; ++c) {
+            R s = Cj[su(N, r, c)];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += AD[r * N + k] * Aj[c * N + k];
+            o.v[E::oC + su(N, r, c)] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = ei_[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += Z[k * N + r] * w[k];
+        o.v[E::oe + r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = r; c < N; ++c) {
+            R s = Ji[su(N, r, c)];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Z[k * N + r] * W[k * N + c];
+            o.v[E::oJ + su(N, r, c)] = s;
+        }
+}
+
+// (b, C) half of Lemma 1 with the carry on the left: c <- c (x) ej.
+// When LL, also returns the pieces of the innovation log-likelihood:
+// logdet(I + C J_j) and w^T D w with w = eta_j - J_j b, D = (I + C J_j)^{-1} C.
+template <int N, typename R, int MODE, bool LL>
+KF_D void apply_fwd(FwdCarry<N, R> &c, const FElem<N, R> &ej, double *ll_logdet, R *ll_wDw) {
+    using E = FElem<N, R>;
+    using CT = FwdCarry<N, R>;
+    const R *b = c.v + CT::ob, *C = c.v + CT::oC;
+    const R *Aj = ej.v + E::oA, *bj = ej.v + E::ob, *Cj = ej.v + E::oC, *ej_ = ej.v + E::oe, *Jj = ej.v + E::oJ;
+    R X[N * N];
+    double ld = 0;
+    inv_I_plus_CJ<N, R, MODE, LL>(C, Jj, X, ld);
+    R D[N * (N + 1) / 2];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int q = r; q < N; ++q) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += X[r * N + k] * C[si(N, k, q)];
+            D[su(N, r, q)] = s;
+        }
+    // u = X (b + C eta_j) = X b + D eta_j
+    R u[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += X[r * N + k] * b[k] + D[si(N, r, k)] * ej_[k];
+        u[r] = s;
+    }
+    if (LL) {
+        R w[N];
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            R s = ej_[r];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s -= Jj[si(N, r, k)] * b[k];
+            w[r] = s;
+        }
+        R q = 0;
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += D[si(N, r, k)] * w[k];
+            q += w[r] * s;
+        }
+        *ll_wDw = q;
+        *ll_logdet = ld;
+    }
+    R AD[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Aj[r * N + k] * D[si(N, k, q)];
+            AD[r * N + q] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = bj[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += Aj[r * N + k] * u[k];
+        c.v[CT::ob + r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int q = r; q < N; ++q) {
+            R s = Cj[su(N, r, q)];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += AD[r * N + k] * Aj[q * N + k];
+            c.v[CT::oC + su(N, r, q)] = s;
+        }
+}
+
+// (eta, J) half of Lemma 1 with the carry on the right: c <- ei (x) c.
+template <int N, typename R, int MODE>
+KF_D void apply_rev(RevCarry<N, R> &c, const FElem<N, R> &ei) {
+    using E = FElem<N, R>;
+    using CT = RevCarry<N, R>;
+    const R *eta = c.v + CT::oe, *J = c.v + CT::oJ;
+    const R *Ai = ei.v + E::oA, *bi = ei.v + E::ob, *Ci = ei.v + E::oC, *ei_ = ei.v + E::oe, *Ji = ei.v + E::oJ;
+    R X[N * N];
+    double ld = 0;
+    inv_I_plus_CJ<N, R, MODE, false>(Ci, J, X, ld);
+    R Z[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += X[r * N + k] * Ai[k * N + q];
+            Z[r * N + q] = s;
+        }
+    R w[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = eta[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s -= J[si(N, r, k)] * bi[k];
+        w[r] = s;
+    }
+    R W[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += J[si(N, r, k)] * Ai[k * N + q];
+            W[r * N + q] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = ei_[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += Z[k * N + r] * w[k];
+        c.v[CT::oe + r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int q = r; q < N; ++q) {
+            R s = Ji[su(N, r, q)];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Z[k * N + r] * W[k * N + q];
+            c.v[CT::oJ + su(N, r, q)] = s;
+        }
+}
+
+// ---------------------------------------------------------------- Lemma 2
+
+// o = ei (x) ej = (E_i E_j, E_i g_j + g_i, E_i L_j E_i^T + L_i).
+template <int N, typename R>
+KF_D void lemma2(const RElem<N, R> &ei, const RElem<N, R> &ej, RElem<N, R> &o) {
+    using E = RElem<N, R>;
+    const R *Ei = ei.v + E::oE, *gi = ei.v + E::og, *Li = ei.v + E::oL;
+    const R *Ej = ej.v + E::oE, *gj = ej.v + E::og, *Lj = ej.v + E::oL;
+    R EL[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Ei[r * N + k] * Lj[si(N, k, c)];
+            EL[r * N + c] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Ei[r * N + k] * Ej[k * N + c];
+            o.v[E::oE + r * N + c] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = gi[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += Ei[r * N + k] * gj[k];
+        o.v[E::og + r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = r; c < N; ++c) {
+            R s = Li[su(N, r, c)];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += EL[r * N + k] * Ei[c * N + k];
+            o.v[E::oL + su(N, r, c)] = s;
+        }
+}
+
+// (g, L) half of Lemma 2 with the carry on the right: c <- ei (x) c.
+template <int N, typename R>
+KF_D void apply_rts(RCarry<N, R> &c, const RElem<N, R> &ei) {
+    using E = RElem<N, R>;
+    using CT = RCarry<N, R>;
+    const R *g = c.v + CT::og, *L = c.v + CT::oL;
+    const R *Ei = ei.v + E::oE, *gi = ei.v + E::og, *Li = ei.v + E::oL;
+    R EL[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Ei[r * N + k] * L[si(N, k, q)];
+            EL[r * N + q] = s;
+        }
+    R gn[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = gi[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += Ei[r * N + k] * g[k];
+        gn[r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int q = r; q < N; ++q) {
+            R s = Li[su(N, r, q)];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += EL[r * N + k] * Ei[q * N + k];
+            c.v[CT::oL + su(N, r, q)] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < N; ++r) c.v[CT::og + r] = gn[r];
+}
+
+// ---------------------------------------------------------------- element construction
+
+// Filtering element a_k from y_k (k 1-based).  k = 1: Eq. pkf_init2
+// (A_1 = 0); k >= 2: Eq. pkf_init1.  eta_k, J_k: Eq. pkf_init3.
+template <int N, typename R>
+KF_D void build_filter_elem(const FiltParams<N, R> &P, int64_t k, const R *yk, FElem<N, R> &e) {
+    using E = FElem<N, R>;
+    const int ny = P.ny;
+    R y[MAXNY];
+#pragma unroll
+    for (int j = 0; j < MAXNY; ++j) y[j] = (j < ny) ? yk[j] : R(0);
+    const bool first = (k == 1);
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R sb = first ? P.c1[r] : R(0), se = 0;
+#pragma unroll
+        for (int j = 0; j < MAXNY; ++j) {
+            if (j < ny) {
+                sb += (first ? P.K1[r * MAXNY + j] : P.K[r * MAXNY + j]) * y[j];
+                se += P.G[r * MAXNY + j] * y[j];
+            }
+        }
+        e.v[E::ob + r] = sb;
+        e.v[E::oe + r] = se;
+    }
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) e.v[E::oA + i] = first ? R(0) : P.A[i];
+#pragma unroll
+    for (int i = 0; i < E::S; ++i) {
+        e.v[E::oC + i] = first ? P.C1[i] : P.C[i];
+        e.v[E::oJ + i] = P.J[i];
+    }
+}
+
+// RTS element from the filtering mean x = xbar_{k|k} and packed covariance
+// Pk = P_{k|k}: Eq. prts_init1 (last = false) or Eq. prts_init2 (last).
+//   U = F P,  Pp = U F^T + Q = L L^T (Cholesky),  E = P F^T Pp^{-1} = (Pp^{-1} U)^T,
+//   g = x - E F x,  L_k = P - E U.
+template <int N, typename R>
+KF_D void build_rts_elem(const FiltParams<N, R> &P, bool last, const R *x, const R *Pk, RElem<N, R> &e) {
+    using E = RElem<N, R>;
+    if (last) {
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) e.v[E::oE + i] = 0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) e.v[E::og + i] = x[i];
+#pragma unroll
+        for (int i = 0; i < E::S; ++i) e.v[E::oL + i] = Pk[i];
+        return;
+    }
+    R U[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += P.F[r * N + k] * Pk[si(N, k, c)];
+            U[r * N + c] = s;
+        }
+    // lower Cholesky factor of Pp, packed by rows (row i holds columns 0..i)
+    R L[N * (N + 1) / 2];
+    R dinv[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            R s = P.Q[su(N, j, i)];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += U[i * N + k] * P.F[j * N + k];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+            if (i == j) {
+                const R d = sqrt(s);
+                L[i * (i + 1) / 2 + i] = d;
+                dinv[i] = R(1) / d;
+            } else {
+                L[i * (i + 1) / 2 + j] = s * dinv[j];
+            }
+        }
+    // Et = Pp^{-1} U: forward then backward substitution, column by column
+    R Et[N * N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        R z[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            R s = U[i * N + c];
+#pragma unroll
+            for (int k = 0; k < i; ++k) s -= L[i * (i + 1) / 2 + k] * z[k];
+            z[i] = s * dinv[i];
+        }
+#pragma unroll
+        for (int i = N - 1; i >= 0; --i) {
+            R s = z[i];
+#pragma unroll
+            for (int k = i + 1; k < N; ++k) s -= L[k * (k + 1) / 2 + i] * Et[k * N + c];
+            Et[i * N + c] = s * dinv[i];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) e.v[E::oE + r * N + c] = Et[c * N + r];
+    R Fx[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += P.F[r * N + k] * x[k];
+        Fx[r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = x[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s -= Et[k * N + r] * Fx[k];
+        e.v[E::og + r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = r; c < N; ++c) {
+            R s = Pk[su(N, r, c)];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s -= Et[k * N + r] * U[k * N + c];
+            e.v[E::oL + su(N, r, c)] = s;
+        }
+}
+
+// Two-filter merge, Eqs. mean_tf_combination / cov_tf_combination:
+//   Xm = (I + P J)^{-1},  ms = Xm (x + P eta),  Ps = Xm P (symmetric).
+template <int N, typename R, int MODE>
+KF_D void tf_merge(const R *x, const R *Pk, const RevCarry<N, R> &c, R *ms, R *Ps_packed) {
+    using CT = RevCarry<N, R>;
+    const R *eta = c.v + CT::oe, *J = c.v + CT::oJ;
+    R X[N * N];
+    double ld = 0;
+    inv_I_plus_CJ<N, R, MODE, false>(Pk, J, X, ld);
+    R t[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = x[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += Pk[si(N, r, k)] * eta[k];
+        t[r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += X[r * N + k] * t[k];
+        ms[r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int q = r; q < N; ++q) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += X[r * N + k] * Pk[si(N, k, q)];
+            Ps_packed[su(N, r, q)] = s;
+        }
+}
+
+}  // namespace kfs

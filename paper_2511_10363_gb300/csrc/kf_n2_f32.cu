@@ -1,0 +1,10 @@
+// kf_n2_f32.cu -- scans for state dimension nx = 2, precision f32.
+#include "kf_launch.cuh"
+
+namespace kfs {
+
+size_t ws_bytes_n2_f32(int op, int scan, int64_t T) { return ws_layout<2, float>(op, scan, T).total; }
+
+cudaError_t launch_n2_f32(const LaunchReq &q) { return launch_typed<2, float, 0, 128>(q); }
+
+}  // namespace kfs

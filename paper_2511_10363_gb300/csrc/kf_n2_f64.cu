@@ -1,0 +1,10 @@
+// kf_n2_f64.cu -- scans for state dimension nx = 2, precision f64.
+#include "kf_launch.cuh"
+
+namespace kfs {
+
+size_t ws_bytes_n2_f64(int op, int scan, int64_t T) { return ws_layout<2, double>(op, scan, T).total; }
+
+cudaError_t launch_n2_f64(const LaunchReq &q) { return launch_typed<2, double, 0, 128>(q); }
+
+}  // namespace kfs

@@ -1,0 +1,10 @@
+// kf_n2_mix.cu -- scans for state dimension nx = 2, precision mix.
+#include "kf_launch.cuh"
+
+namespace kfs {
+
+size_t ws_bytes_n2_mix(int op, int scan, int64_t T) { return ws_layout<2, float>(op, scan, T).total; }
+
+cudaError_t launch_n2_mix(const LaunchReq &q) { return launch_typed<2, float, 1, 128>(q); }
+
+}  // namespace kfs

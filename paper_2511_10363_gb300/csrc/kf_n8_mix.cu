@@ -1,0 +1,10 @@
+// kf_n8_mix.cu -- scans for state dimension nx = 8, precision mix.
+#include "kf_launch.cuh"
+
+namespace kfs {
+
+size_t ws_bytes_n8_mix(int op, int scan, int64_t T) { return ws_layout<8, float>(op, scan, T).total; }
+
+cudaError_t launch_n8_mix(const LaunchReq &q) { return launch_typed<8, float, 1, 128>(q); }
+
+}  // namespace kfs

@@ -1,0 +1,356 @@
+// kf_problems.cuh -- the three scans of arXiv 2511.10363 written as policies
+// for the generic scan kernels, in SCAN ORDER: position p = 0, 1, ... is the
+// order in which the scan accumulates.  combine(x, y) receives x earlier in
+// scan order; apply(c, e) extends a carry by the next element in scan order.
+//
+//   FilterFwd : Alg. pkf   -- forward scan of a_1..a_T under Lemma 1,
+//               carry (b, C), extraction xbar_{k|k} = b_k^+, P_{k|k} = C_k^+,
+//               plus the innovation log-likelihood.
+//   TfRev     : Alg. ptf   -- reversed scan of (a_2, ..., a_T, e) under
+//               Lemma 1, carry (eta, J), extraction eta_{k|k+1:T}, J_{k|k+1:T},
+//               fused with the two-filter merge.
+//   RtsRev    : Alg. prts  -- reversed scan of (E, g, L) under Lemma 2,
+//               carry (g, L), extraction xbar_{k|T} = g_k^+, P_{k|T} = L_k^+.
+//
+// Sequences: a call scans one sequence or a concatenation of independent
+// sequences ("segments").  No segment flags are needed: the operator resets
+// by itself at a boundary.  A forward prefix that reaches a segment's a_1
+// has A = 0 there, so its (b, C) no longer depends on anything before; a
+// reversed RTS suffix that reaches a segment's last element has E = 0; and
+// the two-filter scan ends each segment with e = (0, 0, 0, 0, 0), the
+// terminal element printed in Alg. ptf, whose (eta, J) = (0, 0) cuts the
+// (eta, J) half off from everything after it.
+#pragma once
+
+#include "kf_math.cuh"
+
+namespace kfs {
+
+// Where the model constants of a position come from.
+template <int N, typename R>
+struct OneSeq {
+    FiltParams<N, R> prm;
+    int64_t T;
+};
+
+template <int N, typename R>
+struct ManySeq {
+    const FiltParams<N, R> *prm;   // [nseg]
+    const int64_t *offsets;        // [nseg + 1], offsets[0] = 0
+    int nseg;
+    int64_t total;
+};
+
+// Tracks the segment of the current position while a thread walks
+// consecutive positions.
+struct SegCursor {
+    int s;
+    int64_t b, e;   // [b, e) global index range of segment s
+};
+
+template <int N, typename R>
+KF_D const FiltParams<N, R> &seg_params(const OneSeq<N, R> &q, const SegCursor &) { return q.prm; }
+template <int N, typename R>
+KF_D const FiltParams<N, R> &seg_params(const ManySeq<N, R> &q, const SegCursor &c) { return q.prm[c.s]; }
+
+template <int N, typename R>
+KF_D int64_t seq_total(const OneSeq<N, R> &q) { return q.T; }
+template <int N, typename R>
+KF_D int64_t seq_total(const ManySeq<N, R> &q) { return q.total; }
+
+template <int N, typename R>
+KF_D SegCursor seg_find(const OneSeq<N, R> &q, int64_t) { return SegCursor{0, 0, q.T}; }
+template <int N, typename R>
+KF_D SegCursor seg_find(const ManySeq<N, R> &q, int64_t g) {
+    int lo = 0, hi = q.nseg - 1;   // last segment with offsets[s] <= g
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(q.offsets + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    return SegCursor{lo, __ldg(q.offsets + lo), __ldg(q.offsets + lo + 1)};
+}
+
+template <int N, typename R>
+KF_D void seg_move(const OneSeq<N, R> &, SegCursor &, int64_t) {}
+template <int N, typename R>
+KF_D void seg_move(const ManySeq<N, R> &q, SegCursor &c, int64_t g) {
+    while (g >= c.e) { ++c.s; c.b = c.e; c.e = __ldg(q.offsets + c.s + 1); }
+    while (g < c.b) { --c.s; c.e = c.b; c.b = __ldg(q.offsets + c.s); }
+}
+
+// Output / intermediate buffers shared by the three problems.
+template <typename R>
+struct KfBufs {
+    const R *y;        // [total][ny]
+    R *mf;             // filter means   [total][N]       (workspace or user)
+    R *Pf;             // filter covs, packed upper [total][S] (workspace)
+    R *mf_user;        // optional user copy of filter means [total][N] (if != mf)
+    R *Pf_user;        // optional full filter covs [total][N][N]
+    R *ms;             // smoothed means [total][N]
+    R *Ps;             // smoothed full covs [total][N][N]
+};
+
+template <int N, typename R>
+KF_D void store_full(R *dst, const R *packed) {
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) dst[r * N + c] = packed[si(N, r, c)];
+}
+
+
+// ---------------------------------------------------------------- call policy
+// nx <= 4: operators are inlined (everything stays in registers).  nx = 8:
+// one element no longer fits in the register file, so each operator is one
+// out-of-line function shared by every call site, which keeps code size and
+// compile time bounded.
+template <int N, typename R, int MODE>
+__device__ __noinline__ void lemma1_ool(const FElem<N, R> &a, const FElem<N, R> &b, FElem<N, R> &o) {
+    lemma1<N, R, MODE>(a, b, o);
+}
+template <int N, typename R, int MODE>
+KF_D void op_lemma1(const FElem<N, R> &a, const FElem<N, R> &b, FElem<N, R> &o) {
+    if constexpr (N >= 8) lemma1_ool<N, R, MODE>(a, b, o); else lemma1<N, R, MODE>(a, b, o);
+}
+template <int N, typename R, int MODE, bool LL>
+__device__ __noinline__ void apply_fwd_ool(FwdCarry<N, R> &c, const FElem<N, R> &e, double *ld, R *q) {
+    apply_fwd<N, R, MODE, LL>(c, e, ld, q);
+}
+template <int N, typename R, int MODE, bool LL>
+KF_D void op_apply_fwd(FwdCarry<N, R> &c, const FElem<N, R> &e, double *ld, R *q) {
+    if constexpr (N >= 8) apply_fwd_ool<N, R, MODE, LL>(c, e, ld, q); else apply_fwd<N, R, MODE, LL>(c, e, ld, q);
+}
+template <int N, typename R, int MODE>
+__device__ __noinline__ void apply_rev_ool(RevCarry<N, R> &c, const FElem<N, R> &e) { apply_rev<N, R, MODE>(c, e); }
+template <int N, typename R, int MODE>
+KF_D void op_apply_rev(RevCarry<N, R> &c, const FElem<N, R> &e) {
+    if constexpr (N >= 8) apply_rev_ool<N, R, MODE>(c, e); else apply_rev<N, R, MODE>(c, e);
+}
+template <int N, typename R>
+__device__ __noinline__ void lemma2_ool(const RElem<N, R> &a, const RElem<N, R> &b, RElem<N, R> &o) { lemma2<N, R>(a, b, o); }
+template <int N, typename R>
+KF_D void op_lemma2(const RElem<N, R> &a, const RElem<N, R> &b, RElem<N, R> &o) {
+    if constexpr (N >= 8) lemma2_ool<N, R>(a, b, o); else lemma2<N, R>(a, b, o);
+}
+template <int N, typename R>
+__device__ __noinline__ void apply_rts_ool(RCarry<N, R> &c, const RElem<N, R> &e) { apply_rts<N, R>(c, e); }
+template <int N, typename R>
+KF_D void op_apply_rts(RCarry<N, R> &c, const RElem<N, R> &e) {
+    if constexpr (N >= 8) apply_rts_ool<N, R>(c, e); else apply_rts<N, R>(c, e);
+}
+template <int N, typename R>
+__device__ __noinline__ void build_rts_ool(const FiltParams<N, R> &P, bool last, const R *x, const R *Pk, RElem<N, R> &e) {
+    build_rts_elem<N, R>(P, last, x, Pk, e);
+}
+template <int N, typename R>
+KF_D void op_build_rts(const FiltParams<N, R> &P, bool last, const R *x, const R *Pk, RElem<N, R> &e) {
+    if constexpr (N >= 8) build_rts_ool<N, R>(P, last, x, Pk, e); else build_rts_elem<N, R>(P, last, x, Pk, e);
+}
+template <int N, typename R, int MODE>
+__device__ __noinline__ void tf_merge_ool(const R *x, const R *Pk, const RevCarry<N, R> &c, R *ms, R *Ps) {
+    tf_merge<N, R, MODE>(x, Pk, c, ms, Ps);
+}
+template <int N, typename R, int MODE>
+KF_D void op_tf_merge(const R *x, const R *Pk, const RevCarry<N, R> &c, R *ms, R *Ps) {
+    if constexpr (N >= 8) tf_merge_ool<N, R, MODE>(x, Pk, c, ms, Ps); else tf_merge<N, R, MODE>(x, Pk, c, ms, Ps);
+}
+
+// ---------------------------------------------------------------- filter (forward)
+
+template <int N, typename Rt, int MODE, class Src>
+struct FilterFwd {
+    using R = Rt;
+    using Elem = FElem<N, R>;
+    using Carry = FwdCarry<N, R>;
+    static constexpr int S = N * (N + 1) / 2;
+    struct Args {
+        Src src;
+        KfBufs<R> buf;
+        int want_ll;
+    };
+    static KF_D int64_t total(const Args &a) { return seq_total(a.src); }
+    static KF_D SegCursor cursor(const Args &a, int64_t p) { return seg_find(a.src, p); }
+    static KF_D void build(const Args &a, int64_t p, SegCursor &cur, Elem &e) {
+        seg_move(a.src, cur, p);
+        const FiltParams<N, R> &P = seg_params(a.src, cur);
+        build_filter_elem<N, R>(P, p - cur.b + 1, a.buf.y + p * P.ny, e);
+    }
+    static KF_D void combine(const Elem &x, const Elem &y, Elem &o) { op_lemma1<N, R, MODE>(x, y, o); }
+    static KF_D void apply(Carry &c, const Elem &e) { op_apply_fwd<N, R, MODE, false>(c, e, nullptr, nullptr); }
+    static KF_D void carry_of(const Elem &e, Carry &c) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) c.v[Carry::ob + i] = e.v[Elem::ob + i];
+#pragma unroll
+        for (int i = 0; i < S; ++i) c.v[Carry::oC + i] = e.v[Elem::oC + i];
+    }
+    static KF_D void emit(const Args &a, int64_t p, const Carry &c) {
+        const R *b = c.v + Carry::ob, *C = c.v + Carry::oC;
+        if (a.buf.mf) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) a.buf.mf[p * N + i] = b[i];
+        }
+        if (a.buf.Pf) {
+#pragma unroll
+            for (int i = 0; i < S; ++i) a.buf.Pf[p * S + i] = C[i];
+        }
+        if (a.buf.mf_user) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) a.buf.mf_user[p * N + i] = b[i];
+        }
+        if (a.buf.Pf_user) store_full<N>(a.buf.Pf_user + p * N * N, C);
+    }
+    // log p(y_k | y_{1:k-1}) from the prefix carry c = s_{k-1} before a_k is
+    // applied.  k = 1: v = y_1 - H xbar_{1|0}, S_1 precomputed.  k >= 2:
+    // S_k = S + HF C F^T H^T, so det S_k = det S det(I + C J) and, with
+    // w = eta_k - J b = F^T H^T S^{-1} v, v^T S_k^{-1} v = v^T S^{-1} v - w^T D w,
+    // D = (I + C J)^{-1} C (matrix determinant lemma and Woodbury identity).
+    static KF_D double step(const Args &a, int64_t p, SegCursor &cur, Carry &c, const Elem &e) {
+        if (!a.want_ll) {
+            apply(c, e);
+            emit(a, p, c);
+            return 0.0;
+        }
+        const FiltParams<N, R> &P = seg_params(a.src, cur);
+        const int ny = P.ny;
+        const R *yk = a.buf.y + p * ny;
+        double ll;
+        if (p == cur.b) {
+            R v[MAXNY];
+#pragma unroll
+            for (int j = 0; j < MAXNY; ++j) v[j] = (j < ny) ? yk[j] - P.Hx1[j] : R(0);
+            R q = 0;
+#pragma unroll
+            for (int i = 0; i < MAXNY; ++i)
+#pragma unroll
+                for (int j = 0; j < MAXNY; ++j)
+                    if (i < ny && j < ny) q += v[i] * P.S1inv[i * MAXNY + j] * v[j];
+            ll = -0.5 * (double(q) + P.llc1);
+            apply(c, e);
+        } else {
+            const R *b = c.v + Carry::ob;
+            R v[MAXNY];
+#pragma unroll
+            for (int j = 0; j < MAXNY; ++j) {
+                R s = (j < ny) ? yk[j] : R(0);
+#pragma unroll
+                for (int k = 0; k < N; ++k) s -= (j < ny) ? P.HF[j * N + k] * b[k] : R(0);
+                v[j] = s;
+            }
+            R q = 0;
+#pragma unroll
+            for (int i = 0; i < MAXNY; ++i)
+#pragma unroll
+                for (int j = 0; j < MAXNY; ++j)
+                    if (i < ny && j < ny) q += v[i] * P.Sinv[i * MAXNY + j] * v[j];
+            double ld;
+            R wDw;
+            op_apply_fwd<N, R, MODE, true>(c, e, &ld, &wDw);
+            ll = -0.5 * (double(q) - double(wDw) + P.llc + ld);
+        }
+        emit(a, p, c);
+        return ll;
+    }
+};
+
+// ---------------------------------------------------------------- two-filter (reverse)
+
+template <int N, typename Rt, int MODE, class Src>
+struct TfRev {
+    using R = Rt;
+    using Elem = FElem<N, R>;
+    using Carry = RevCarry<N, R>;
+    static constexpr int S = N * (N + 1) / 2;
+    struct Args {
+        Src src;
+        KfBufs<R> buf;
+        int want_ll;
+    };
+    static KF_D int64_t total(const Args &a) { return seq_total(a.src); }
+    static KF_D SegCursor cursor(const Args &a, int64_t p) { return seg_find(a.src, seq_total(a.src) - 1 - p); }
+    // position p holds b_k = a_{k+1} (k < T_s) or e = 0 (k = T_s), where
+    // g = total-1-p is the global index of time k.
+    static KF_D void build(const Args &a, int64_t p, SegCursor &cur, Elem &e) {
+        const int64_t g = seq_total(a.src) - 1 - p;
+        seg_move(a.src, cur, g);
+        if (g == cur.e - 1) {
+            set_zero(e);
+            return;
+        }
+        const FiltParams<N, R> &P = seg_params(a.src, cur);
+        build_filter_elem<N, R>(P, g - cur.b + 2, a.buf.y + (g + 1) * P.ny, e);
+    }
+    static KF_D void combine(const Elem &x, const Elem &y, Elem &o) { op_lemma1<N, R, MODE>(y, x, o); }
+    static KF_D void apply(Carry &c, const Elem &e) { op_apply_rev<N, R, MODE>(c, e); }
+    static KF_D void carry_of(const Elem &e, Carry &c) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) c.v[Carry::oe + i] = e.v[Elem::oe + i];
+#pragma unroll
+        for (int i = 0; i < S; ++i) c.v[Carry::oJ + i] = e.v[Elem::oJ + i];
+    }
+    static KF_D void emit(const Args &a, int64_t p, const Carry &c) {
+        const int64_t g = seq_total(a.src) - 1 - p;
+        R x[N], Pk[S], ms[N], Ps[S];
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = a.buf.mf[g * N + i];
+#pragma unroll
+        for (int i = 0; i < S; ++i) Pk[i] = a.buf.Pf[g * S + i];
+        op_tf_merge<N, R, MODE>(x, Pk, c, ms, Ps);
+#pragma unroll
+        for (int i = 0; i < N; ++i) a.buf.ms[g * N + i] = ms[i];
+        store_full<N>(a.buf.Ps + g * N * N, Ps);
+    }
+    static KF_D double step(const Args &a, int64_t p, SegCursor &, Carry &c, const Elem &e) {
+        apply(c, e);
+        emit(a, p, c);
+        return 0.0;
+    }
+};
+
+// ---------------------------------------------------------------- RTS (reverse)
+
+template <int N, typename Rt, class Src>
+struct RtsRev {
+    using R = Rt;
+    using Elem = RElem<N, R>;
+    using Carry = RCarry<N, R>;
+    static constexpr int S = N * (N + 1) / 2;
+    struct Args {
+        Src src;
+        KfBufs<R> buf;
+        int want_ll;
+    };
+    static KF_D int64_t total(const Args &a) { return seq_total(a.src); }
+    static KF_D SegCursor cursor(const Args &a, int64_t p) { return seg_find(a.src, seq_total(a.src) - 1 - p); }
+    static KF_D void build(const Args &a, int64_t p, SegCursor &cur, Elem &e) {
+        const int64_t g = seq_total(a.src) - 1 - p;
+        seg_move(a.src, cur, g);
+        const FiltParams<N, R> &P = seg_params(a.src, cur);
+        R x[N], Pk[S];
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = a.buf.mf[g * N + i];
+#pragma unroll
+        for (int i = 0; i < S; ++i) Pk[i] = a.buf.Pf[g * S + i];
+        op_build_rts<N, R>(P, g == cur.e - 1, x, Pk, e);
+    }
+    static KF_D void combine(const Elem &x, const Elem &y, Elem &o) { op_lemma2<N, R>(y, x, o); }
+    static KF_D void apply(Carry &c, const Elem &e) { op_apply_rts<N, R>(c, e); }
+    static KF_D void carry_of(const Elem &e, Carry &c) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) c.v[Carry::og + i] = e.v[Elem::og + i];
+#pragma unroll
+        for (int i = 0; i < S; ++i) c.v[Carry::oL + i] = e.v[Elem::oL + i];
+    }
+    static KF_D void emit(const Args &a, int64_t p, const Carry &c) {
+        const int64_t g = seq_total(a.src) - 1 - p;
+#pragma unroll
+        for (int i = 0; i < N; ++i) a.buf.ms[g * N + i] = c.v[Carry::og + i];
+        store_full<N>(a.buf.Ps + g * N * N, c.v + Carry::oL);
+    }
+    static KF_D double step(const Args &a, int64_t p, SegCursor &, Carry &c, const Elem &e) {
+        apply(c, e);
+        emit(a, p, c);
+        return 0.0;
+    }
+};
+
+}  // namespace kfs

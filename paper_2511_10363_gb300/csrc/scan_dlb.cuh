@@ -1,0 +1,347 @@
+// scan_dlb.cuh -- single-pass scan with decoupled look-back, generic over a
+// problem policy (kf_problems.cuh).
+//
+// One CTA scans one tile of THREADS * K consecutive scan positions:
+//   1. take a tile ticket (atomic counter), so every tile that a CTA waits
+//      for was claimed by a CTA that is already running;
+//   2. each thread builds its K elements and folds them (full operator);
+//   3. a warp Kogge-Stone scan (shuffles) and a scan of the warp aggregates
+//      give every thread its exclusive prefix inside the tile and the tile
+//      aggregate, which is published (flag 1);
+//   4. look-back: every thread takes V predecessor tiles, waits (bounded)
+//      until each has published, and the CTA finds the nearest predecessor
+//      that already published its inclusive prefix (flag 2); the aggregates
+//      after it are reduced in order by the whole CTA (thread folds, warp
+//      shuffle tree, warp-0 tree) and applied to that inclusive carry;
+//   5. the tile's inclusive carry is published (flag 2);
+//   6. each thread walks its K elements again, extending the carry one
+//      element at a time with the one-sided operator, and emits its outputs
+//      (extraction fused into the scan).
+// The launcher keeps the number of tiles <= THREADS * V, so one look-back
+// window always covers every predecessor.
+//
+// Every wait is bounded by a wall-clock limit (%globaltimer); on time-out the
+// CTA records KF_ERR_TIMEOUT in the status word and returns; other CTAs see
+// the status word and stop waiting too.
+#pragma once
+
+#include "kf_problems.cuh"
+
+namespace kfs {
+
+struct DlbCtl {
+    int *counters;         // [0] tile ticket, [1] finished-tile count
+    int *flags;            // [ntiles] 0 empty, 1 aggregate, 2 inclusive
+    void *agg;             // [ntiles][Elem::SIZE]
+    void *incl;            // [ntiles][Carry::SIZE]
+    double *ll_part;       // [ntiles] per-tile log-likelihood partial sums
+    double *ll_out;        // final log-likelihood (nullable)
+    int *status;           // device status word
+    int64_t timeout_ns;    // bound of every wait
+    int ntiles;
+    int K;                 // positions per thread
+    int inject_skip_tile;  // test hook: this tile never publishes (-1: none)
+};
+
+constexpr int KF_STATUS_TIMEOUT = 5;
+
+KF_D int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+KF_D void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+KF_D int ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+KF_D uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait until *f != 0; returns the flag, or 0 when the wait ran out or
+// another CTA already failed.
+KF_D int wait_flag(const int *f, const DlbCtl &ctl) {
+    int v = ld_acquire(f);
+    if (v) return v;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        __nanosleep(64);
+        v = ld_acquire(f);
+        if (v) return v;
+        if (ld_relaxed(ctl.status) != 0) return 0;
+        if (int64_t(global_ns() - t0) > ctl.timeout_ns) {
+            atomicCAS(ctl.status, 0, KF_STATUS_TIMEOUT);
+            return 0;
+        }
+    }
+}
+
+template <class X>
+KF_D void shfl_up_x(const X &in, X &out, int d) {
+#pragma unroll
+    for (int i = 0; i < X::SIZE; ++i) out.v[i] = __shfl_up_sync(0xffffffffu, in.v[i], d);
+}
+template <class X>
+KF_D void shfl_down_x(const X &in, X &out, int d) {
+#pragma unroll
+    for (int i = 0; i < X::SIZE; ++i) out.v[i] = __shfl_down_sync(0xffffffffu, in.v[i], d);
+}
+template <class X, typename R>
+KF_D void load_cg(X &x, const R *src) {
+#pragma unroll
+    for (int i = 0; i < X::SIZE; ++i) x.v[i] = __ldcg(src + i);
+}
+
+template <class P, int THREADS, int V>
+__global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant__ typename P::Args args,
+                                                           const DlbCtl ctl) {
+    using R = typename P::R;
+    using Elem = typename P::Elem;
+    using Carry = typename P::Carry;
+    constexpr int NW = THREADS / 32, ES = Elem::SIZE, CS = Carry::SIZE;
+    __shared__ R s_wx[NW][ES];     // warp-exclusive prefixes inside the tile
+    __shared__ R s_red[NW][ES];    // tile aggregate / look-back reduction
+    __shared__ R s_carry[CS];      // tile-exclusive carry
+    __shared__ double s_ll[NW];
+    __shared__ int s_tile, s_qstar, s_abort, s_last;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_tile = atomicAdd(ctl.counters, 1);
+        s_qstar = -1;
+        s_abort = 0;
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= ctl.ntiles || tile == ctl.inject_skip_tile) return;
+    const int64_t total = P::total(args);
+    const int64_t start = (int64_t(tile) * THREADS + tid) * ctl.K;
+    const int64_t end = start + ctl.K < total ? start + ctl.K : total;
+
+    // ---- 2. thread fold
+    Elem agg;
+    if (start < end) {
+        SegCursor cur = P::cursor(args, start);
+        P::build(args, start, cur, agg);
+        for (int64_t p = start + 1; p < end; ++p) {
+            Elem e, t;
+            P::build(args, p, cur, e);
+            P::combine(agg, e, t);
+            agg = t;
+        }
+    } else {
+        set_identity(agg);
+    }
+
+    // ---- 3. warp scan, warp-aggregate scan
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        Elem o, t;
+        shfl_up_x(agg, o, s);
+        if (lane >= s) {
+            P::combine(o, agg, t);
+            agg = t;
+        }
+    }
+    Elem lex;
+    shfl_up_x(agg, lex, 1);
+    if (lane == 31) {
+#pragma unroll
+        for (int i = 0; i < ES; ++i) s_wx[warp][i] = agg.v[i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        Elem w;
+        if (lane < NW) {
+#pragma unroll
+            for (int i = 0; i < ES; ++i) w.v[i] = s_wx[lane][i];
+        } else {
+            set_identity(w);
+        }
+#pragma unroll
+        for (int s = 1; s < NW; s <<= 1) {
+            Elem o, t;
+            shfl_up_x(w, o, s);
+            if (lane >= s) {
+                P::combine(o, w, t);
+                w = t;
+            }
+        }
+        Elem wx;
+        shfl_up_x(w, wx, 1);
+        if (lane == 0) set_identity(wx);
+        __syncwarp();
+        if (lane < NW) {
+#pragma unroll
+            for (int i = 0; i < ES; ++i) s_wx[lane][i] = wx.v[i];
+        }
+        if (lane == NW - 1) {
+#pragma unroll
+            for (int i = 0; i < ES; ++i) s_red[0][i] = w.v[i];
+        }
+    }
+    __syncthreads();
+    Elem tagg;
+#pragma unroll
+    for (int i = 0; i < ES; ++i) tagg.v[i] = s_red[0][i];
+
+    // publish the tile aggregate (tile 0 publishes its inclusive prefix directly)
+    if (tile > 0) {
+        R *dst = static_cast<R *>(ctl.agg) + int64_t(tile) * ES;
+        for (int i = tid; i < ES; i += THREADS) dst[i] = tagg.v[i];
+        __threadfence();
+    }
+    __syncthreads();
+    if (tile > 0 && tid == 0) st_release(ctl.flags + tile, 1);
+
+    // ---- 4. look-back
+    Carry tc;
+    set_zero(tc);
+    if (tile > 0) {
+        int fl[V];
+        int qloc = -1;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int q = tile - 1 - (tid * V + v);
+            fl[v] = 0;
+            if (q >= 0) {
+                fl[v] = wait_flag(ctl.flags + q, ctl);
+                if (fl[v] == 0) s_abort = 1;
+                if (fl[v] == 2 && q > qloc) qloc = q;
+            }
+        }
+        if (qloc >= 0) atomicMax(&s_qstar, qloc);
+        __syncthreads();
+        if (s_abort) return;
+        const int qstar = s_qstar;
+        // fold the aggregates of my predecessors after qstar, earliest first
+        Elem x;
+        bool have = false;
+#pragma unroll
+        for (int v = V - 1; v >= 0; --v) {
+            const int q = tile - 1 - (tid * V + v);
+            if (q > qstar) {
+                Elem a;
+                load_cg(a, static_cast<const R *>(ctl.agg) + int64_t(q) * ES);
+                if (!have) {
+                    x = a;
+                    have = true;
+                } else {
+                    Elem t;
+                    P::combine(x, a, t);
+                    x = t;
+                }
+            }
+        }
+        if (!have) set_identity(x);
+        // lane l covers later tiles than lane l+1: suffix reduction to lane 0
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            Elem o, t;
+            shfl_down_x(x, o, s);
+            if (lane + s < 32) {
+                P::combine(o, x, t);
+                x = t;
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < ES; ++i) s_red[warp][i] = x.v[i];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            Elem y;
+            if (lane < NW) {
+#pragma unroll
+                for (int i = 0; i < ES; ++i) y.v[i] = s_red[lane][i];
+            } else {
+                set_identity(y);
+            }
+#pragma unroll
+            for (int s = 1; s < NW; s <<= 1) {
+                Elem o, t;
+                shfl_down_x(y, o, s);
+                if (lane + s < NW) {
+                    P::combine(o, y, t);
+                    y = t;
+                }
+            }
+            if (qstar >= 0) load_cg(tc, static_cast<const R *>(ctl.incl) + int64_t(qstar) * CS);
+            P::apply(tc, y);
+        }
+    }
+    // ---- 5. publish the inclusive carry
+    if (warp == 0) {
+        Carry inc = tc;
+        P::apply(inc, tagg);
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < CS; ++i) s_carry[i] = tc.v[i];
+            R *dst = static_cast<R *>(ctl.incl) + int64_t(tile) * CS;
+#pragma unroll
+            for (int i = 0; i < CS; ++i) dst[i] = inc.v[i];
+            __threadfence();
+            st_release(ctl.flags + tile, 2);
+        }
+    }
+    __syncthreads();
+
+    // ---- 6. carries and the fused extraction pass
+    Carry c;
+#pragma unroll
+    for (int i = 0; i < CS; ++i) c.v[i] = s_carry[i];
+    if (warp > 0) {
+        Elem wx;
+#pragma unroll
+        for (int i = 0; i < ES; ++i) wx.v[i] = s_wx[warp][i];
+        P::apply(c, wx);
+    }
+    if (lane > 0) P::apply(c, lex);
+    double ll = 0.0;
+    if (start < end) {
+        SegCursor cur = P::cursor(args, start);
+        for (int64_t p = start; p < end; ++p) {
+            Elem e;
+            P::build(args, p, cur, e);
+            ll += P::step(args, p, cur, c, e);
+        }
+    }
+
+    // ---- log-likelihood: fixed-order reduction per tile, then over tiles
+    if (ctl.ll_out) {
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) ll += __shfl_down_sync(0xffffffffu, ll, s);
+        if (lane == 0) s_ll[warp] = ll;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NW; ++w) t += s_ll[w];
+            ctl.ll_part[tile] = t;
+            __threadfence();
+            s_last = (atomicAdd(ctl.counters + 1, 1) == ctl.ntiles - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            double t = 0.0;
+            for (int i = tid; i < ctl.ntiles; i += THREADS) t += __ldcg(ctl.ll_part + i);
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) t += __shfl_down_sync(0xffffffffu, t, s);
+            if (lane == 0) s_ll[warp] = t;
+            __syncthreads();
+            if (tid == 0) {
+                double u = 0.0;
+                for (int w = 0; w < NW; ++w) u += s_ll[w];
+                *ctl.ll_out = u;
+            }
+        }
+    }
+}
+
+}  // namespace kfs

@@ -1,0 +1,105 @@
+"""CPU-only checks of the C-ABI library: it loads, exports every function
+declared in include/*.h, and its host-side argument checks and workspace
+sizing work without a GPU (no compute call is made)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2511_10363_gb300 as kf
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(kf_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_10363_gb300 import build
+    build.build()
+    return kf.lib()
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for required in ("kf_filter", "kf_rts_smooth", "kf_two_filter_smooth", "kf_workspace_size",
+                     "kf_sync_status", "kf_status_string"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version(lib):
+    for s in range(8):
+        assert kf.kf_status_string(s)
+    assert "sm_103a" in kf.kf_version()
+
+
+FAKE = ctypes.c_void_p(1 << 20)   # never dereferenced: every call below fails its host checks
+
+
+def call_filter(model, T=16, y=FAKE, prec=1, scan=1, m=FAKE):
+    mm = kf.Model(model)
+    return kf.lib().kf_filter(ctypes.byref(mm.c), T, y, prec, scan, m, None, None, None, None)
+
+
+def test_argument_errors(lib):
+    good = W.cv_model()
+    assert call_filter(good, T=0) == 1                       # T >= 1
+    assert call_filter(good, y=None) == 1                    # y required
+    assert call_filter(good, m=None) == 1                    # output required
+    assert call_filter(good, prec=7) == 1                    # bad enum
+    assert call_filter(good, scan=9) == 1
+    assert call_filter(good, y=ctypes.c_void_p((1 << 20) + 2)) == 1   # misaligned
+    bad = dict(good)
+    bad["F"] = np.eye(3)
+    bad["H"] = np.zeros((2, 3))
+    bad["Q"] = np.eye(3)
+    bad["P0"] = np.eye(3)
+    bad["m0"] = np.zeros(3)
+    assert call_filter(bad) == 1                             # nx = 3 unsupported
+    r = dict(good)
+    r["R"] = -np.eye(2)
+    assert call_filter(r) == 2                               # R not PD
+    q = dict(good)
+    q["Q"] = good["Q"] - 0.5 * np.eye(4)
+    assert call_filter(q) == 2                               # Q not PSD
+    a = dict(good)
+    a["P0"] = np.array([[1, 2, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0], [0, 0, 0, 1.0]])
+    assert call_filter(a) == 2                               # P0 not symmetric
+
+
+def test_workspace_size(lib):
+    s1 = kf.kf_workspace_size("filter", 4, 2, 1 << 20, "fp32", "dlb")
+    s2 = kf.kf_workspace_size("rts", 4, 2, 1 << 20, "fp32", "dlb")
+    s3 = kf.kf_workspace_size("rts", 4, 2, 1 << 20, "fp64", "dlb")
+    s4 = kf.kf_workspace_size("rts", 4, 2, 1 << 20, "fp32", "blelloch")
+    assert 0 < s1 < s2 < s3 and s2 < s4
+    # the smoothers keep the filter means and packed covariances: (4 + 10) words per step
+    assert s2 - s1 >= (1 << 20) * 14 * 4
+    assert kf.kf_workspace_size("rts", 3, 2, 100) == 0
+    assert kf.kf_workspace_size("rts", 4, 9, 100) == 0
+
+
+def test_options(lib):
+    assert kf.kf_get_option("wait_timeout_ns") == 10 ** 9
+    with pytest.raises(kf.KfError):
+        kf.kf_set_option("wait_timeout_ns", 10)
+    kf.kf_set_option("wait_timeout_ns", 5 * 10 ** 8)
+    assert kf.kf_get_option("wait_timeout_ns") == 5 * 10 ** 8
+    kf.kf_set_option("wait_timeout_ns", 10 ** 9)
