@@ -199,7 +199,25 @@ static size_t g_ws_bytes[64];
 static int *g_status[64];
 static std::atomic<int64_t> g_opt[8] = {1000000000LL, -1, 0, 0, 0, 0, 0, 0};
 
+// KFSCAN_DEBUG=1 in the environment logs each stage of a call to stderr.
+bool debug_on() {
+    static int on = -1;
+    if (on < 0) {
+        const char *v = getenv("KFSCAN_DEBUG");
+        on = (v && v[0] && v[0] != '0') ? 1 : 0;
+    }
+    return on == 1;
+}
+#define KF_DBG(...)                                  \
+    do {                                             \
+        if (debug_on()) {                            \
+            fprintf(stderr, "[kfscan] " __VA_ARGS__); \
+            fflush(stderr);                          \
+        }                                            \
+    } while (0)
+
 static kf_status_t from_cuda(cudaError_t e) {
+    if (e != cudaSuccess) KF_DBG("CUDA error %d: %s\n", int(e), cudaGetErrorString(e));
     if (e == cudaSuccess) return KF_OK;
     if (e == cudaErrorMemoryAllocation) return KF_ERR_OOM;
     return KF_ERR_CUDA;
@@ -302,6 +320,8 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
     if (workspace && !aligned(workspace, 256)) return KF_ERR_ARG;
     HostModel hm;
     s = precompute(md, &hm);
+    KF_DBG("op=%d nx=%d ny=%d T=%lld prec=%d scan=%d precompute=%d\n", op, md->nx, md->ny, (long long)T, int(prec),
+           q.scan, int(s));
     if (s != KF_OK) return s;
     q.hm = &hm;
     q.loglik = loglik;
@@ -311,6 +331,7 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
     q.k_override = int(g_opt[KF_OPT_POSITIONS_PER_THREAD].load());
     q.threads = int(g_opt[KF_OPT_THREADS].load());
     s = device_status_word(&q.status);
+    KF_DBG("status word %p (%d)\n", (void *)q.status, int(s));
     if (s != KF_OK) return s;
     const size_t need = ws_bytes_dispatch(md->nx, op, q.prec, q.scan, T);
     if (workspace) {
@@ -319,7 +340,10 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
         s = library_workspace(need, &q.ws);
         if (s != KF_OK) return s;
     }
-    return from_cuda(launch_dispatch(q));
+    KF_DBG("workspace %p (%zu bytes needed)\n", q.ws, need);
+    const cudaError_t e = launch_dispatch(q);
+    KF_DBG("launched: %d\n", int(e));
+    return from_cuda(e);
 }
 
 }  // namespace kfs

@@ -53,6 +53,7 @@ struct LaunchReq {
     int threads;         // CTA size of the decoupled look-back scan (0: default)
 };
 
+bool debug_on();   // KFSCAN_DEBUG set in the environment
 size_t ws_bytes_dispatch(int nx, int op, int prec, int scan, int64_t T);
 cudaError_t launch_dispatch(const LaunchReq &q);
 

@@ -3,6 +3,8 @@
 #pragma once
 
 #include "kf_host.h"
+#include <stdio.h>
+
 #include "scan_levels.cuh"
 
 namespace kfs {
@@ -50,7 +52,15 @@ template <class P, int THREADS, int V>
 static int max_resident_tiles(int device) {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dlb_scan_kernel<P, THREADS, V>, THREADS, 0);
+    if (debug_on()) {
+        fprintf(stderr, "[kfscan] querying kernel attributes\n");
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, dlb_scan_kernel<P, THREADS, V>);
+        fprintf(stderr, "[kfscan] attrs: %d regs=%d local=%zu shared=%zu maxthr=%d\n", int(e), fa.numRegs,
+                fa.localSizeBytes, fa.sharedSizeBytes, fa.maxThreadsPerBlock);
+    }
+    cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dlb_scan_kernel<P, THREADS, V>, THREADS, 0);
+    if (debug_on()) fprintf(stderr, "[kfscan] occupancy: %d per_sm=%d sms=%d\n", int(oe), per_sm, sms);
     if (per_sm < 1) per_sm = 1;
     return sms * per_sm;
 }
@@ -133,6 +143,7 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
                            const LaunchReq &q, double *ll_out) {
     int dev = 0;
     cudaGetDevice(&dev);
+    if (debug_on()) fprintf(stderr, "[kfscan] run_dlb\n");
     const int64_t total = P::total(args);
     const TilePlan tp = plan_tiles(total, THREADS, THREADS * V, max_resident_tiles<P, THREADS, V>(dev), q.k_override);
     DlbCtl ctl;
@@ -148,9 +159,17 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
     ctl.K = tp.K;
     ctl.inject_skip_tile = q.inject_skip_tile;
     cudaError_t e = cudaMemsetAsync(ctl.counters, 0, sizeof(int) * (2 + tp.ntiles), q.stream);
+    if (debug_on()) fprintf(stderr, "[kfscan] dlb: total=%lld tiles=%d K=%d threads=%d memset=%d\n",
+                            (long long)total, tp.ntiles, tp.K, THREADS, int(e));
     if (e != cudaSuccess) return e;
     dlb_scan_kernel<P, THREADS, V><<<tp.ntiles, THREADS, 0, q.stream>>>(args, ctl);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (debug_on()) {
+        fprintf(stderr, "[kfscan] dlb launch: %d (%s)\n", int(e), cudaGetErrorString(e));
+        cudaError_t s = cudaStreamSynchronize(q.stream);
+        fprintf(stderr, "[kfscan] dlb sync: %d (%s)\n", int(s), cudaGetErrorString(s));
+    }
+    return e;
 }
 
 static inline int lv_grid(int64_t work, int threads) {

@@ -54,9 +54,9 @@ template <int N, typename R>
 KF_D const FiltParams<N, R> &seg_params(const ManySeq<N, R> &q, const SegCursor &c) { return q.prm[c.s]; }
 
 template <int N, typename R>
-KF_D int64_t seq_total(const OneSeq<N, R> &q) { return q.T; }
+KF_HD int64_t seq_total(const OneSeq<N, R> &q) { return q.T; }
 template <int N, typename R>
-KF_D int64_t seq_total(const ManySeq<N, R> &q) { return q.total; }
+KF_HD int64_t seq_total(const ManySeq<N, R> &q) { return q.total; }
 
 template <int N, typename R>
 KF_D SegCursor seg_find(const OneSeq<N, R> &q, int64_t) { return SegCursor{0, 0, q.T}; }
@@ -168,7 +168,7 @@ struct FilterFwd {
         KfBufs<R> buf;
         int want_ll;
     };
-    static KF_D int64_t total(const Args &a) { return seq_total(a.src); }
+    static KF_HD int64_t total(const Args &a) { return seq_total(a.src); }
     static KF_D SegCursor cursor(const Args &a, int64_t p) { return seg_find(a.src, p); }
     static KF_D void build(const Args &a, int64_t p, SegCursor &cur, Elem &e) {
         seg_move(a.src, cur, p);
@@ -265,7 +265,7 @@ struct TfRev {
         KfBufs<R> buf;
         int want_ll;
     };
-    static KF_D int64_t total(const Args &a) { return seq_total(a.src); }
+    static KF_HD int64_t total(const Args &a) { return seq_total(a.src); }
     static KF_D SegCursor cursor(const Args &a, int64_t p) { return seg_find(a.src, seq_total(a.src) - 1 - p); }
     // position p holds b_k = a_{k+1} (k < T_s) or e = 0 (k = T_s), where
     // g = total-1-p is the global index of time k.
@@ -319,7 +319,7 @@ struct RtsRev {
         KfBufs<R> buf;
         int want_ll;
     };
-    static KF_D int64_t total(const Args &a) { return seq_total(a.src); }
+    static KF_HD int64_t total(const Args &a) { return seq_total(a.src); }
     static KF_D SegCursor cursor(const Args &a, int64_t p) { return seg_find(a.src, seq_total(a.src) - 1 - p); }
     static KF_D void build(const Args &a, int64_t p, SegCursor &cur, Elem &e) {
         const int64_t g = seq_total(a.src) - 1 - p;
