@@ -153,6 +153,31 @@ typedef enum {
 kf_status_t kf_set_option(kf_option_t opt, int64_t value);
 int64_t kf_get_option(kf_option_t opt); /* -1 for an unknown option */
 
+/* Kernel accounting (diagnostics for benchmarks).  The library counts every
+ * kernel it launches, by kind.  While timing is enabled it also brackets each
+ * scan (one kernel for the decoupled look-back scan; the whole level-by-level
+ * launch sequence otherwise) with two CUDA events on the call's stream.
+ * kf_timing_read waits for the recorded events of that kind and returns the
+ * number of kernels launched and the milliseconds accumulated since the last
+ * kf_timing_reset. */
+typedef enum {
+    KF_KERNEL_FILTER_SCAN = 0,   /* forward scan, Lemma 1 (Alg. pkf)              */
+    KF_KERNEL_RTS_SCAN = 1,      /* reversed scan, Lemma 2 (Alg. prts)            */
+    KF_KERNEL_TF_SCAN = 2,       /* reversed scan of (a_2..a_T, e) + merge (ptf)  */
+    KF_KERNEL_FILTER_LEVELS = 3, /* the same three, run by a level algorithm      */
+    KF_KERNEL_RTS_LEVELS = 4,
+    KF_KERNEL_TF_LEVELS = 5,
+    KF_KERNEL_KINDS = 6
+} kf_kernel_t;
+kf_status_t kf_timing_enable(int on);
+kf_status_t kf_timing_reset(void);
+kf_status_t kf_timing_read(kf_kernel_t kind, int64_t *launches, double *total_ms);
+
+/* Measures the FP32 (fp64 = 0) or FP64 (fp64 = 1) fused multiply-add
+ * throughput of the current device with a kernel of independent FMA chains
+ * on every SM, and returns it in FLOP/s (an FMA counts as 2).  Synchronous. */
+kf_status_t kf_measure_fma_peak(int fp64, double *flops_per_second);
+
 #ifdef __cplusplus
 }
 #endif

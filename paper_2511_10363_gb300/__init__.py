@@ -70,6 +70,11 @@ def lib():
         L.kf_status_string.argtypes = [i]
         L.kf_status_string.restype = ctypes.c_char_p
         L.kf_version.restype = ctypes.c_char_p
+        for f in ("kf_timing_enable", "kf_timing_reset", "kf_timing_read", "kf_measure_fma_peak"):
+            getattr(L, f).restype = ctypes.c_int
+        L.kf_timing_enable.argtypes = [i]
+        L.kf_timing_read.argtypes = [i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+        L.kf_measure_fma_peak.argtypes = [i, ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
 
@@ -194,3 +199,56 @@ def kf_set_option(name, value):
 
 def kf_get_option(name):
     return int(lib().kf_get_option(OPTIONS[name]))
+
+
+def kf_timing_enable(on=True):
+    _check(lib().kf_timing_enable(1 if on else 0), "kf_timing_enable")
+
+
+def kf_timing_reset():
+    _check(lib().kf_timing_reset(), "kf_timing_reset")
+
+
+def timing_read(kind):
+    """(kernel launches, total ms) of one kf_kernel_t kind since the last reset."""
+    n = ctypes.c_int64(0)
+    ms = ctypes.c_double(0)
+    _check(lib().kf_timing_read(int(kind), ctypes.byref(n), ctypes.byref(ms)), "kf_timing_read")
+    return int(n.value), float(ms.value)
+
+
+def measure_fma_peak(fp64=False):
+    """Measured FMA throughput of the current device in FLOP/s."""
+    v = ctypes.c_double(0)
+    _check(lib().kf_measure_fma_peak(1 if fp64 else 0, ctypes.byref(v)), "kf_measure_fma_peak")
+    return float(v.value)
+
+
+def rts_smooth_host(model, y_host, precision, scan, ms_host, Ps_host, ll_host=None, workspace=None, op="rts",
+                    y_dev=None, ms_dev=None, Ps_dev=None, ll_dev=None, stream=None):
+    """Smooth a sequence held in (pinned) host memory: copy y to the device,
+    run kf_rts_smooth (or kf_two_filter_smooth with op="tf"), and copy the
+    smoothed means, covariances and log-likelihood back, all enqueued on one
+    stream.  Device staging buffers may be passed in to avoid allocation."""
+    import torch
+    T = y_host.shape[0]
+    m = _as_model(model)
+    dt = dtype_of(precision)
+    if y_dev is None:
+        y_dev = torch.empty(y_host.shape, dtype=dt, device="cuda")
+    if ms_dev is None:
+        ms_dev = torch.empty((T, m.nx), dtype=dt, device="cuda")
+    if Ps_dev is None:
+        Ps_dev = torch.empty((T, m.nx, m.nx), dtype=dt, device="cuda")
+    if ll_host is not None and ll_dev is None:
+        ll_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    y_dev.copy_(y_host, non_blocking=True)
+    fn = lib().kf_rts_smooth if op == "rts" else lib().kf_two_filter_smooth
+    rc = fn(ctypes.byref(m.c), T, _ptr(y_dev), PRECISIONS[precision], SCANS[scan], _ptr(ms_dev), _ptr(Ps_dev),
+            None, None, _ptr(ll_dev) if ll_host is not None else None, _ptr(workspace), _stream(stream))
+    _check(rc, "kf_rts_smooth")
+    ms_host.copy_(ms_dev, non_blocking=True)
+    Ps_host.copy_(Ps_dev, non_blocking=True)
+    if ll_host is not None:
+        ll_host.copy_(ll_dev, non_blocking=True)
+    return ms_host, Ps_host, ll_host

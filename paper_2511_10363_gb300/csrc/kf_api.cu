@@ -216,6 +216,52 @@ bool debug_on() {
         }                                            \
     } while (0)
 
+// ---------------------------------------------------------------- kernel accounting
+
+static std::atomic<int64_t> g_launches[KF_KERNEL_KINDS];
+static std::atomic<int> g_timing{0};
+struct TimingEntry {
+    int kind;
+    cudaEvent_t a, b;
+};
+static std::mutex g_tmu;
+static TimingEntry *g_tent = nullptr;
+static size_t g_tn = 0, g_tcap = 0;
+static double g_tms[KF_KERNEL_KINDS];
+static int64_t g_tlaunch0[KF_KERNEL_KINDS];
+
+void count_launches(int kind, int n) { g_launches[kind] += n; }
+bool timing_on() { return g_timing.load() != 0; }
+void timing_record(int, cudaStream_t s, cudaEvent_t *ev) {
+    if (cudaEventCreate(ev) != cudaSuccess) { *ev = nullptr; return; }
+    cudaEventRecord(*ev, s);
+}
+void timing_commit(int kind, cudaStream_t s, cudaEvent_t start) {
+    cudaEvent_t stop;
+    if (cudaEventCreate(&stop) != cudaSuccess) return;
+    cudaEventRecord(stop, s);
+    std::lock_guard<std::mutex> lk(g_tmu);
+    if (g_tn == g_tcap) {
+        size_t cap = g_tcap ? 2 * g_tcap : 256;
+        TimingEntry *n = static_cast<TimingEntry *>(realloc(g_tent, cap * sizeof(TimingEntry)));
+        if (!n) return;
+        g_tent = n;
+        g_tcap = cap;
+    }
+    g_tent[g_tn++] = TimingEntry{kind, start, stop};
+}
+static void timing_drain() {   // caller holds g_tmu
+    for (size_t i = 0; i < g_tn; ++i) {
+        float ms = 0;
+        if (cudaEventSynchronize(g_tent[i].b) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, g_tent[i].a, g_tent[i].b) == cudaSuccess)
+            g_tms[g_tent[i].kind] += ms;
+        cudaEventDestroy(g_tent[i].a);
+        cudaEventDestroy(g_tent[i].b);
+    }
+    g_tn = 0;
+}
+
 static kf_status_t from_cuda(cudaError_t e) {
     if (e != cudaSuccess) KF_DBG("CUDA error %d: %s\n", int(e), cudaGetErrorString(e));
     if (e == cudaSuccess) return KF_OK;
@@ -346,6 +392,55 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
     return from_cuda(e);
 }
 
+// Independent FMA chains: 8 per thread, so each warp keeps the FMA pipe busy
+// without depending on neighbours; the result is stored only when it equals
+// an impossible value, which keeps the chains live.
+template <typename T>
+__global__ void fma_peak_kernel(T a, T b, int iters, T *sink) {
+    T x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = T(threadIdx.x + i);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+    }
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+    if (s == T(-1.2345e30)) *sink = s;
+}
+
+template <typename T>
+static kf_status_t fma_peak(double *out) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return KF_ERR_CUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    T *sink = nullptr;
+    if (cudaMalloc(&sink, sizeof(T)) != cudaSuccess) return KF_ERR_OOM;
+    const int threads = 256, blocks = sms * 8;
+    const int iters = sizeof(T) == 4 ? 1 << 16 : 1 << 11;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0);
+        fma_peak_kernel<T><<<blocks, threads>>>(T(0.999999), T(1e-7), iters, sink);
+        cudaEventRecord(e1);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double flops = 2.0 * 8.0 * double(iters) * blocks * threads;
+        if (rep > 0 && ms > 0) best = fmax(best, flops / (ms * 1e-3));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (cudaGetLastError() != cudaSuccess || best == 0) return KF_ERR_CUDA;
+    *out = best;
+    return KF_OK;
+}
+
 }  // namespace kfs
 
 using namespace kfs;
@@ -409,6 +504,35 @@ kf_status_t kf_sync_status(void *stream) {
         return kf_status_t(v);
     }
     return KF_OK;
+}
+
+kf_status_t kf_timing_enable(int on) {
+    g_timing.store(on ? 1 : 0);
+    return KF_OK;
+}
+
+kf_status_t kf_timing_reset(void) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    timing_drain();
+    for (int k = 0; k < KF_KERNEL_KINDS; ++k) {
+        g_tms[k] = 0;
+        g_tlaunch0[k] = g_launches[k].load();
+    }
+    return KF_OK;
+}
+
+kf_status_t kf_timing_read(kf_kernel_t kind, int64_t *launches, double *total_ms) {
+    if (kind < 0 || kind >= KF_KERNEL_KINDS) return KF_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    timing_drain();
+    if (launches) *launches = g_launches[kind].load() - g_tlaunch0[kind];
+    if (total_ms) *total_ms = g_tms[kind];
+    return KF_OK;
+}
+
+kf_status_t kf_measure_fma_peak(int fp64, double *flops_per_second) {
+    if (!flops_per_second) return KF_ERR_ARG;
+    return fp64 ? fma_peak<double>(flops_per_second) : fma_peak<float>(flops_per_second);
 }
 
 kf_status_t kf_set_option(kf_option_t opt, int64_t value) {

@@ -54,6 +54,12 @@ struct LaunchReq {
 };
 
 bool debug_on();   // KFSCAN_DEBUG set in the environment
+
+// kernel accounting (kf_timing_* in kfscan.h)
+void count_launches(int kind, int n);
+bool timing_on();
+void timing_record(int kind, cudaStream_t s, cudaEvent_t *ev);          // start event
+void timing_commit(int kind, cudaStream_t s, cudaEvent_t start);        // stop event
 size_t ws_bytes_dispatch(int nx, int op, int prec, int scan, int64_t T);
 cudaError_t launch_dispatch(const LaunchReq &q);
 

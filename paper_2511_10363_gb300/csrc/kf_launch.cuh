@@ -162,8 +162,12 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
     if (debug_on()) fprintf(stderr, "[kfscan] dlb: total=%lld tiles=%d K=%d threads=%d memset=%d\n",
                             (long long)total, tp.ntiles, tp.K, THREADS, int(e));
     if (e != cudaSuccess) return e;
+    cudaEvent_t t0 = nullptr;
+    if (timing_on()) timing_record(P::KIND, q.stream, &t0);
     dlb_scan_kernel<P, THREADS, V><<<tp.ntiles, THREADS, 0, q.stream>>>(args, ctl);
     e = cudaGetLastError();
+    count_launches(P::KIND, 1);
+    if (t0) timing_commit(P::KIND, q.stream, t0);
     if (debug_on()) {
         fprintf(stderr, "[kfscan] dlb launch: %d (%s)\n", int(e), cudaGetErrorString(e));
         cudaError_t s = cudaStreamSynchronize(q.stream);
@@ -195,7 +199,11 @@ static cudaError_t run_levels(const typename P::Args &args, char *ws, size_t ctl
     R *b = L.lv_b ? reinterpret_cast<R *>(ws + L.lv_b) : nullptr;
     cudaStream_t st = q.stream;
     R *res = a;
+    cudaEvent_t t0 = nullptr;
+    if (timing_on()) timing_record(3 + P::KIND, st, &t0);
+    int nl = 0;
     if (q.scan == KF_SCAN_HS_I) {
+        nl = 1 + Lg;
         lv_build<P><<<lv_grid(Tp, LT), LT, 0, st>>>(args, a, nullptr, Tp);
         R *src = a, *dst = b;
         for (int d = 0; d < Lg; ++d) {
@@ -204,17 +212,22 @@ static cudaError_t run_levels(const typename P::Args &args, char *ws, size_t ctl
         }
         res = src;
     } else if (q.scan == KF_SCAN_BLELLOCH_I) {
+        nl = 4 + 2 * Lg;
         lv_build<P><<<lv_grid(Tp, LT), LT, 0, st>>>(args, a, b, Tp);
         for (int d = 0; d < Lg; ++d) lv_upsweep<P><<<lv_grid(Tp >> (d + 1), LT), LT, 0, st>>>(a, Tp, d);
         lv_set_identity<P><<<1, 32, 0, st>>>(a, Tp, Tp - 1);
         for (int d = Lg - 1; d >= 0; --d) lv_blelloch_down<P><<<lv_grid(Tp >> (d + 1), LT), LT, 0, st>>>(a, Tp, d);
         lv_blelloch_final<P><<<lv_grid(Tp, LT), LT, 0, st>>>(a, b, Tp);
     } else {  // Ladner-Fischer
+        nl = 1 + Lg;
         lv_build<P><<<lv_grid(Tp, LT), LT, 0, st>>>(args, a, nullptr, Tp);
         for (int d = 0; d < Lg; ++d) lv_upsweep<P><<<lv_grid(Tp >> (d + 1), LT), LT, 0, st>>>(a, Tp, d);
         for (int d = Lg - 1; d >= 0; --d) {
             const int64_t n = (Tp >> (d + 1)) - 1;
-            if (n > 0) lv_lafi_down<P><<<lv_grid(n, LT), LT, 0, st>>>(a, Tp, d);
+            if (n > 0) {
+                lv_lafi_down<P><<<lv_grid(n, LT), LT, 0, st>>>(a, Tp, d);
+                ++nl;
+            }
         }
     }
     int *counter = reinterpret_cast<int *>(ws + ctl_off);
@@ -223,6 +236,8 @@ static cudaError_t run_levels(const typename P::Args &args, char *ws, size_t ctl
     int g = lv_grid(total, LT);
     if (g > KF_MAX_TILES) g = KF_MAX_TILES;
     lv_extract<P, LT><<<g, LT, 0, st>>>(args, res, Tp, reinterpret_cast<double *>(ws + L.llpart), counter, ll_out);
+    count_launches(3 + P::KIND, nl + 1);
+    if (t0) timing_commit(3 + P::KIND, st, t0);
     return cudaGetLastError();
 }
 

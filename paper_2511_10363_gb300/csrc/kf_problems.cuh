@@ -159,6 +159,7 @@ KF_D void op_tf_merge(const R *x, const R *Pk, const RevCarry<N, R> &c, R *ms, R
 
 template <int N, typename Rt, int MODE, class Src>
 struct FilterFwd {
+    static constexpr int KIND = 0;
     using R = Rt;
     using Elem = FElem<N, R>;
     using Carry = FwdCarry<N, R>;
@@ -256,6 +257,7 @@ struct FilterFwd {
 
 template <int N, typename Rt, int MODE, class Src>
 struct TfRev {
+    static constexpr int KIND = 2;
     using R = Rt;
     using Elem = FElem<N, R>;
     using Carry = RevCarry<N, R>;
@@ -310,6 +312,7 @@ struct TfRev {
 
 template <int N, typename Rt, class Src>
 struct RtsRev {
+    static constexpr int KIND = 1;
     using R = Rt;
     using Elem = RElem<N, R>;
     using Carry = RCarry<N, R>;
