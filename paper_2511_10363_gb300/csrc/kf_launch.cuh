@@ -48,18 +48,19 @@ void to_params(const HostModel &h, FiltParams<N, R> &p) {
 
 // ---------------------------------------------------------------- tile plan
 
-template <class P, int THREADS, int V>
-static int max_resident_tiles(int device) {
+template <class P, int THREADS, int V, int C>
+static int max_resident_tiles(int device, int smem) {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (debug_on()) {
         fprintf(stderr, "[kfscan] querying kernel attributes\n");
         cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, dlb_scan_kernel<P, THREADS, V>);
+        cudaError_t e = cudaFuncGetAttributes(&fa, dlb_scan_kernel<P, THREADS, V, C>);
         fprintf(stderr, "[kfscan] attrs: %d regs=%d local=%zu shared=%zu maxthr=%d\n", int(e), fa.numRegs,
                 fa.localSizeBytes, fa.sharedSizeBytes, fa.maxThreadsPerBlock);
     }
-    cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dlb_scan_kernel<P, THREADS, V>, THREADS, 0);
+    cudaError_t oe =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dlb_scan_kernel<P, THREADS, V, C>, THREADS, smem);
     if (debug_on()) fprintf(stderr, "[kfscan] occupancy: %d per_sm=%d sms=%d\n", int(oe), per_sm, sms);
     if (per_sm < 1) per_sm = 1;
     return sms * per_sm;
@@ -95,10 +96,10 @@ static TilePlan plan_tiles(int64_t total, int threads, int window, int resident,
 //   agg    : KF_MAX_TILES * max element size * sizeof(R)
 //   incl   : KF_MAX_TILES * max carry size * sizeof(R)
 //   llpart : KF_MAX_TILES doubles
-//   mf, Pf : filter means [T][N] and packed covariances [T][S] (smoothers)
+//   frec   : filter records [T][FRec::SIZE] (smoothers)
 //   lv_a, lv_b : level-scan element buffers [ES][Tpad] (level algorithms)
 struct WsLayout {
-    size_t ctl_f, ctl_r, agg, incl, llpart, mf, Pf, lv_a, lv_b, total;
+    size_t ctl_f, ctl_r, agg, incl, llpart, frec, lv_a, lv_b, total;
 };
 
 static inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -111,7 +112,6 @@ static inline int64_t next_pow2(int64_t t) {
 
 template <int N, typename R>
 WsLayout ws_layout(int op, int scan, int64_t T) {
-    constexpr int S = N * (N + 1) / 2;
     constexpr int ES = FElem<N, R>::SIZE;  // >= RElem size
     constexpr int CS = FwdCarry<N, R>::SIZE;
     WsLayout L;
@@ -122,10 +122,9 @@ WsLayout ws_layout(int op, int scan, int64_t T) {
     L.agg = o; o += al256(size_t(KF_MAX_TILES) * ES * sizeof(R));
     L.incl = o; o += al256(size_t(KF_MAX_TILES) * CS * sizeof(R));
     L.llpart = o; o += al256(size_t(KF_MAX_TILES) * sizeof(double));
-    L.mf = L.Pf = L.lv_a = L.lv_b = 0;
+    L.frec = L.lv_a = L.lv_b = 0;
     if (op != KF_OP_FILTER_I) {
-        L.mf = o; o += al256(size_t(T) * N * sizeof(R));
-        L.Pf = o; o += al256(size_t(T) * S * sizeof(R));
+        L.frec = o; o += al256(size_t(T) * FRec<N, R>::SIZE * sizeof(R));
     }
     if (scan != KF_SCAN_DLB_I) {
         const int64_t Tp = next_pow2(T);
@@ -138,15 +137,57 @@ WsLayout ws_layout(int op, int scan, int64_t T) {
 
 // ---------------------------------------------------------------- one scan
 
+// Time steps per lane staged at once: as many as keep one CTA's staging
+// buffers within 96 KB (at most 8).
+template <class P, int THREADS>
+constexpr int stage_chunk() {
+    constexpr int bpp = 32 * (2 * P::IN_REC + P::O1 + P::O2 + P::O3) * int(sizeof(typename P::R));
+    constexpr int c = (96 * 1024) / ((THREADS / 32) * bpp);
+    return c < 1 ? 1 : (c > 8 ? 8 : c);
+}
+
+// Per-warp shared-memory layout of the staging buffers actually used.
+template <class P, int C>
+static void stage_layout(const typename P::Args &args, DlbCtl &ctl) {
+    using R = typename P::R;
+    int o = 0;
+    auto take = [&](int bytes) {
+        const int at = o;
+        o += (bytes + 15) & ~15;
+        return at;
+    };
+    ctl.sm_in0 = ctl.sm_in1 = -1;
+    if (P::IN_REC) {
+        ctl.sm_in0 = take(WarpStage<C, (P::IN_REC ? P::IN_REC : 1), R>::BYTES);
+        ctl.sm_in1 = take(WarpStage<C, (P::IN_REC ? P::IN_REC : 1), R>::BYTES);
+    }
+    const int sizes[3] = {WarpStage<C, (P::O1 ? P::O1 : 1), R>::BYTES, WarpStage<C, (P::O2 ? P::O2 : 1), R>::BYTES,
+                          WarpStage<C, (P::O3 ? P::O3 : 1), R>::BYTES};
+    const int recs[3] = {P::O1, P::O2, P::O3};
+    for (int i = 0; i < 3; ++i) ctl.sm_out[i] = (recs[i] && P::out_arr(args, i)) ? take(sizes[i]) : -1;
+    ctl.sm_warp = o;
+}
+
 template <class P, int THREADS, int V>
 static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_off, const WsLayout &L,
                            const LaunchReq &q, double *ll_out) {
+    constexpr int C = stage_chunk<P, THREADS>();
     int dev = 0;
     cudaGetDevice(&dev);
     if (debug_on()) fprintf(stderr, "[kfscan] run_dlb\n");
     const int64_t total = P::total(args);
-    const TilePlan tp = plan_tiles(total, THREADS, THREADS * V, max_resident_tiles<P, THREADS, V>(dev), q.k_override);
     DlbCtl ctl;
+    stage_layout<P, C>(args, ctl);
+    const int smem = ctl.sm_warp * (THREADS / 32);
+    static int attr_smem = 0;   // dynamic shared memory already allowed for this instantiation
+    if (smem > attr_smem) {
+        cudaError_t e = cudaFuncSetAttribute(dlb_scan_kernel<P, THREADS, V, C>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_smem = smem;
+    }
+    const TilePlan tp =
+        plan_tiles(total, THREADS, THREADS * V, max_resident_tiles<P, THREADS, V, C>(dev, smem), q.k_override);
     ctl.counters = reinterpret_cast<int *>(ws + ctl_off);
     ctl.flags = ctl.counters + 2;
     ctl.agg = ws + L.agg;
@@ -159,12 +200,13 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
     ctl.K = tp.K;
     ctl.inject_skip_tile = q.inject_skip_tile;
     cudaError_t e = cudaMemsetAsync(ctl.counters, 0, sizeof(int) * (2 + tp.ntiles), q.stream);
-    if (debug_on()) fprintf(stderr, "[kfscan] dlb: total=%lld tiles=%d K=%d threads=%d memset=%d\n",
-                            (long long)total, tp.ntiles, tp.K, THREADS, int(e));
+    if (debug_on())
+        fprintf(stderr, "[kfscan] dlb: total=%lld tiles=%d K=%d C=%d threads=%d smem=%d memset=%d\n",
+                (long long)total, tp.ntiles, tp.K, C, THREADS, smem, int(e));
     if (e != cudaSuccess) return e;
     cudaEvent_t t0 = nullptr;
     if (timing_on()) timing_record(P::KIND, q.stream, &t0);
-    dlb_scan_kernel<P, THREADS, V><<<tp.ntiles, THREADS, 0, q.stream>>>(args, ctl);
+    dlb_scan_kernel<P, THREADS, V, C><<<tp.ntiles, THREADS, smem, q.stream>>>(args, ctl);
     e = cudaGetLastError();
     count_launches(P::KIND, 1);
     if (t0) timing_commit(P::KIND, q.stream, t0);
@@ -261,13 +303,7 @@ static cudaError_t launch_typed(const LaunchReq &q) {
     buf.y = static_cast<const R *>(q.y);
     buf.ms = static_cast<R *>(q.ms);
     buf.Ps = static_cast<R *>(q.Ps);
-    if (q.op == KF_OP_FILTER_I) {
-        buf.mf = nullptr;
-        buf.Pf = nullptr;
-    } else {
-        buf.mf = reinterpret_cast<R *>(ws + L.mf);
-        buf.Pf = reinterpret_cast<R *>(ws + L.Pf);
-    }
+    buf.frec = (q.op == KF_OP_FILTER_I) ? nullptr : reinterpret_cast<R *>(ws + L.frec);
     buf.mf_user = static_cast<R *>(q.mf_user);
     buf.Pf_user = static_cast<R *>(q.Pf_user);
 

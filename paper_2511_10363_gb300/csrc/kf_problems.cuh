@@ -78,14 +78,21 @@ KF_D void seg_move(const ManySeq<N, R> &q, SegCursor &c, int64_t g) {
     while (g < c.b) { --c.s; c.e = c.b; c.b = __ldg(q.offsets + c.s); }
 }
 
+// Filter record: the forward pass hands (xbar_{k|k}, P_{k|k}) to the smoother
+// passes as one 16-byte aligned record [m (N), packed P (S), padding].
+template <int N, typename R>
+struct FRec {
+    static constexpr int S = N * (N + 1) / 2, Q = 16 / int(sizeof(R));
+    static constexpr int SIZE = ((N + S + Q - 1) / Q) * Q;
+};
+
 // Output / intermediate buffers shared by the three problems.
 template <typename R>
 struct KfBufs {
     const R *y;        // [total][ny]
-    R *mf;             // filter means   [total][N]       (workspace or user)
-    R *Pf;             // filter covs, packed upper [total][S] (workspace)
-    R *mf_user;        // optional user copy of filter means [total][N] (if != mf)
-    R *Pf_user;        // optional full filter covs [total][N][N]
+    R *frec;           // filter records [total][FRec::SIZE] (workspace; null for a plain filter call)
+    R *mf_user;        // optional filter means [total][N]
+    R *Pf_user;        // optional full filter covariances [total][N][N]
     R *ms;             // smoothed means [total][N]
     R *Ps;             // smoothed full covs [total][N][N]
 };
@@ -97,7 +104,6 @@ KF_D void store_full(R *dst, const R *packed) {
 #pragma unroll
         for (int c = 0; c < N; ++c) dst[r * N + c] = packed[si(N, r, c)];
 }
-
 
 // ---------------------------------------------------------------- call policy
 // nx <= 4: operators are inlined (everything stays in registers).  nx = 8:
@@ -155,23 +161,35 @@ KF_D void op_tf_merge(const R *x, const R *Pk, const RevCarry<N, R> &c, R *ms, R
     if constexpr (N >= 8) tf_merge_ool<N, R, MODE>(x, Pk, c, ms, Ps); else tf_merge<N, R, MODE>(x, Pk, c, ms, Ps);
 }
 
-// ---------------------------------------------------------------- filter (forward)
+// ---------------------------------------------------------------- problems
+//
+// Interface used by the scan kernels.  Positions p are in scan order; the
+// global index of p is g = p (forward) or g = total - 1 - p (reverse).  Each
+// problem reads at most one per-position input record array (IN_REC
+// elements, 0 = none) and writes up to three output record arrays (O1, O2,
+// O3 elements per record, 0 = none).  build() and step() receive record
+// pointers, which point either into a warp's shared-memory staging buffer or
+// straight into device memory.
 
 template <int N, typename Rt, int MODE, class Src>
 struct FilterFwd {
     static constexpr int KIND = 0;
+    static constexpr bool REV = false;
     using R = Rt;
     using Elem = FElem<N, R>;
     using Carry = FwdCarry<N, R>;
     static constexpr int S = N * (N + 1) / 2;
+    static constexpr int IN_REC = 0, O1 = FRec<N, R>::SIZE, O2 = N, O3 = N * N;
     struct Args {
         Src src;
         KfBufs<R> buf;
         int want_ll;
     };
     static KF_HD int64_t total(const Args &a) { return seq_total(a.src); }
+    static KF_HD const R *in_arr(const Args &) { return nullptr; }
+    static KF_HD R *out_arr(const Args &a, int i) { return i == 0 ? a.buf.frec : i == 1 ? a.buf.mf_user : a.buf.Pf_user; }
     static KF_D SegCursor cursor(const Args &a, int64_t p) { return seg_find(a.src, p); }
-    static KF_D void build(const Args &a, int64_t p, SegCursor &cur, Elem &e) {
+    static KF_D void build(const Args &a, int64_t p, SegCursor &cur, const R *, Elem &e) {
         seg_move(a.src, cur, p);
         const FiltParams<N, R> &P = seg_params(a.src, cur);
         build_filter_elem<N, R>(P, p - cur.b + 1, a.buf.y + p * P.ny, e);
@@ -184,31 +202,30 @@ struct FilterFwd {
 #pragma unroll
         for (int i = 0; i < S; ++i) c.v[Carry::oC + i] = e.v[Elem::oC + i];
     }
-    static KF_D void emit(const Args &a, int64_t p, const Carry &c) {
+    static KF_D void emit(const Args &, const Carry &c, const R *, R *o1, R *o2, R *o3) {
         const R *b = c.v + Carry::ob, *C = c.v + Carry::oC;
-        if (a.buf.mf) {
+        if (o1) {
 #pragma unroll
-            for (int i = 0; i < N; ++i) a.buf.mf[p * N + i] = b[i];
-        }
-        if (a.buf.Pf) {
+            for (int i = 0; i < N; ++i) o1[i] = b[i];
 #pragma unroll
-            for (int i = 0; i < S; ++i) a.buf.Pf[p * S + i] = C[i];
+            for (int i = 0; i < S; ++i) o1[N + i] = C[i];
         }
-        if (a.buf.mf_user) {
+        if (o2) {
 #pragma unroll
-            for (int i = 0; i < N; ++i) a.buf.mf_user[p * N + i] = b[i];
+            for (int i = 0; i < N; ++i) o2[i] = b[i];
         }
-        if (a.buf.Pf_user) store_full<N>(a.buf.Pf_user + p * N * N, C);
+        if (o3) store_full<N>(o3, C);
     }
     // log p(y_k | y_{1:k-1}) from the prefix carry c = s_{k-1} before a_k is
     // applied.  k = 1: v = y_1 - H xbar_{1|0}, S_1 precomputed.  k >= 2:
     // S_k = S + HF C F^T H^T, so det S_k = det S det(I + C J) and, with
     // w = eta_k - J b = F^T H^T S^{-1} v, v^T S_k^{-1} v = v^T S^{-1} v - w^T D w,
     // D = (I + C J)^{-1} C (matrix determinant lemma and Woodbury identity).
-    static KF_D double step(const Args &a, int64_t p, SegCursor &cur, Carry &c, const Elem &e) {
+    static KF_D double step(const Args &a, int64_t p, SegCursor &cur, Carry &c, const Elem &e, const R *in, R *o1,
+                            R *o2, R *o3) {
         if (!a.want_ll) {
             apply(c, e);
-            emit(a, p, c);
+            emit(a, c, in, o1, o2, o3);
             return 0.0;
         }
         const FiltParams<N, R> &P = seg_params(a.src, cur);
@@ -248,7 +265,7 @@ struct FilterFwd {
             op_apply_fwd<N, R, MODE, true>(c, e, &ld, &wDw);
             ll = -0.5 * (double(q) - double(wDw) + P.llc + ld);
         }
-        emit(a, p, c);
+        emit(a, c, in, o1, o2, o3);
         return ll;
     }
 };
@@ -258,20 +275,24 @@ struct FilterFwd {
 template <int N, typename Rt, int MODE, class Src>
 struct TfRev {
     static constexpr int KIND = 2;
+    static constexpr bool REV = true;
     using R = Rt;
     using Elem = FElem<N, R>;
     using Carry = RevCarry<N, R>;
     static constexpr int S = N * (N + 1) / 2;
+    static constexpr int IN_REC = FRec<N, R>::SIZE, O1 = N, O2 = N * N, O3 = 0;
     struct Args {
         Src src;
         KfBufs<R> buf;
         int want_ll;
     };
     static KF_HD int64_t total(const Args &a) { return seq_total(a.src); }
+    static KF_HD const R *in_arr(const Args &a) { return a.buf.frec; }
+    static KF_HD R *out_arr(const Args &a, int i) { return i == 0 ? a.buf.ms : i == 1 ? a.buf.Ps : nullptr; }
     static KF_D SegCursor cursor(const Args &a, int64_t p) { return seg_find(a.src, seq_total(a.src) - 1 - p); }
     // position p holds b_k = a_{k+1} (k < T_s) or e = 0 (k = T_s), where
     // g = total-1-p is the global index of time k.
-    static KF_D void build(const Args &a, int64_t p, SegCursor &cur, Elem &e) {
+    static KF_D void build(const Args &a, int64_t p, SegCursor &cur, const R *, Elem &e) {
         const int64_t g = seq_total(a.src) - 1 - p;
         seg_move(a.src, cur, g);
         if (g == cur.e - 1) {
@@ -289,21 +310,22 @@ struct TfRev {
 #pragma unroll
         for (int i = 0; i < S; ++i) c.v[Carry::oJ + i] = e.v[Elem::oJ + i];
     }
-    static KF_D void emit(const Args &a, int64_t p, const Carry &c) {
-        const int64_t g = seq_total(a.src) - 1 - p;
+    // merge with the filter record (Eqs. mean_tf_combination / cov_tf_combination)
+    static KF_D void emit(const Args &, const Carry &c, const R *in, R *o1, R *o2, R *) {
         R x[N], Pk[S], ms[N], Ps[S];
 #pragma unroll
-        for (int i = 0; i < N; ++i) x[i] = a.buf.mf[g * N + i];
+        for (int i = 0; i < N; ++i) x[i] = in[i];
 #pragma unroll
-        for (int i = 0; i < S; ++i) Pk[i] = a.buf.Pf[g * S + i];
+        for (int i = 0; i < S; ++i) Pk[i] = in[N + i];
         op_tf_merge<N, R, MODE>(x, Pk, c, ms, Ps);
 #pragma unroll
-        for (int i = 0; i < N; ++i) a.buf.ms[g * N + i] = ms[i];
-        store_full<N>(a.buf.Ps + g * N * N, Ps);
+        for (int i = 0; i < N; ++i) o1[i] = ms[i];
+        store_full<N>(o2, Ps);
     }
-    static KF_D double step(const Args &a, int64_t p, SegCursor &, Carry &c, const Elem &e) {
+    static KF_D double step(const Args &a, int64_t, SegCursor &, Carry &c, const Elem &e, const R *in, R *o1, R *o2,
+                            R *o3) {
         apply(c, e);
-        emit(a, p, c);
+        emit(a, c, in, o1, o2, o3);
         return 0.0;
     }
 };
@@ -313,26 +335,30 @@ struct TfRev {
 template <int N, typename Rt, class Src>
 struct RtsRev {
     static constexpr int KIND = 1;
+    static constexpr bool REV = true;
     using R = Rt;
     using Elem = RElem<N, R>;
     using Carry = RCarry<N, R>;
     static constexpr int S = N * (N + 1) / 2;
+    static constexpr int IN_REC = FRec<N, R>::SIZE, O1 = N, O2 = N * N, O3 = 0;
     struct Args {
         Src src;
         KfBufs<R> buf;
         int want_ll;
     };
     static KF_HD int64_t total(const Args &a) { return seq_total(a.src); }
+    static KF_HD const R *in_arr(const Args &a) { return a.buf.frec; }
+    static KF_HD R *out_arr(const Args &a, int i) { return i == 0 ? a.buf.ms : i == 1 ? a.buf.Ps : nullptr; }
     static KF_D SegCursor cursor(const Args &a, int64_t p) { return seg_find(a.src, seq_total(a.src) - 1 - p); }
-    static KF_D void build(const Args &a, int64_t p, SegCursor &cur, Elem &e) {
+    static KF_D void build(const Args &a, int64_t p, SegCursor &cur, const R *in, Elem &e) {
         const int64_t g = seq_total(a.src) - 1 - p;
         seg_move(a.src, cur, g);
         const FiltParams<N, R> &P = seg_params(a.src, cur);
         R x[N], Pk[S];
 #pragma unroll
-        for (int i = 0; i < N; ++i) x[i] = a.buf.mf[g * N + i];
+        for (int i = 0; i < N; ++i) x[i] = in[i];
 #pragma unroll
-        for (int i = 0; i < S; ++i) Pk[i] = a.buf.Pf[g * S + i];
+        for (int i = 0; i < S; ++i) Pk[i] = in[N + i];
         op_build_rts<N, R>(P, g == cur.e - 1, x, Pk, e);
     }
     static KF_D void combine(const Elem &x, const Elem &y, Elem &o) { op_lemma2<N, R>(y, x, o); }
@@ -343,17 +369,34 @@ struct RtsRev {
 #pragma unroll
         for (int i = 0; i < S; ++i) c.v[Carry::oL + i] = e.v[Elem::oL + i];
     }
-    static KF_D void emit(const Args &a, int64_t p, const Carry &c) {
-        const int64_t g = seq_total(a.src) - 1 - p;
+    static KF_D void emit(const Args &, const Carry &c, const R *, R *o1, R *o2, R *) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) a.buf.ms[g * N + i] = c.v[Carry::og + i];
-        store_full<N>(a.buf.Ps + g * N * N, c.v + Carry::oL);
+        for (int i = 0; i < N; ++i) o1[i] = c.v[Carry::og + i];
+        store_full<N>(o2, c.v + Carry::oL);
     }
-    static KF_D double step(const Args &a, int64_t p, SegCursor &, Carry &c, const Elem &e) {
+    static KF_D double step(const Args &a, int64_t, SegCursor &, Carry &c, const Elem &e, const R *in, R *o1, R *o2,
+                            R *o3) {
         apply(c, e);
-        emit(a, p, c);
+        emit(a, c, in, o1, o2, o3);
         return 0.0;
     }
 };
+
+// Direct (unstaged) record pointers of position p, for the level kernels.
+template <class P>
+KF_D int64_t global_index(const typename P::Args &a, int64_t p) {
+    return P::REV ? P::total(a) - 1 - p : p;
+}
+template <class P>
+KF_D const typename P::R *in_rec_direct(const typename P::Args &a, int64_t g) {
+    const typename P::R *b = P::in_arr(a);
+    return (P::IN_REC && b) ? b + g * P::IN_REC : nullptr;
+}
+template <class P>
+KF_D typename P::R *out_rec_direct(const typename P::Args &a, int i, int64_t g) {
+    constexpr int sz[3] = {P::O1, P::O2, P::O3};
+    typename P::R *b = P::out_arr(a, i);
+    return (sz[i] && b) ? b + g * sz[i] : nullptr;
+}
 
 }  // namespace kfs

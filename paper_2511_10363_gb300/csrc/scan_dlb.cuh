@@ -26,6 +26,7 @@
 #pragma once
 
 #include "kf_problems.cuh"
+#include "stage.cuh"
 
 namespace kfs {
 
@@ -41,6 +42,9 @@ struct DlbCtl {
     int ntiles;
     int K;                 // positions per thread
     int inject_skip_tile;  // test hook: this tile never publishes (-1: none)
+    // per-warp dynamic shared memory: byte offsets of the staging buffers
+    // (input double buffer, three outputs; -1 = absent) and the warp stride
+    int sm_in0, sm_in1, sm_out[3], sm_warp;
 };
 
 constexpr int KF_STATUS_TIMEOUT = 5;
@@ -98,7 +102,17 @@ KF_D void load_cg(X &x, const R *src) {
     for (int i = 0; i < X::SIZE; ++i) x.v[i] = __ldcg(src + i);
 }
 
-template <class P, int THREADS, int V>
+// Global record index of scan position p, and the first record of the
+// C-record segment that holds positions [p0, p0 + C) (record order is the
+// global order, so a reverse scan walks its segment backwards).
+template <class P>
+KF_D int64_t gidx(int64_t total, int64_t p) { return P::REV ? total - 1 - p : p; }
+template <class P, int C>
+KF_D int64_t seg_first(int64_t total, int64_t p0) { return P::REV ? total - p0 - C : p0; }
+template <class P, int C>
+KF_D int seg_slot(int c) { return P::REV ? C - 1 - c : c; }
+
+template <class P, int THREADS, int V, int C>
 __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant__ typename P::Args args,
                                                            const DlbCtl ctl) {
     using R = typename P::R;
@@ -124,19 +138,52 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
     const int64_t start = (int64_t(tile) * THREADS + tid) * ctl.K;
     const int64_t end = start + ctl.K < total ? start + ctl.K : total;
 
-    // ---- 2. thread fold
+    extern __shared__ __align__(16) unsigned char dsm[];
+    unsigned char *wsm = dsm + warp * ctl.sm_warp;
+    unsigned char *const in0 = P::IN_REC ? wsm + ctl.sm_in0 : nullptr;
+    unsigned char *const in1 = P::IN_REC ? wsm + ctl.sm_in1 : nullptr;
+    const int nchunks = (ctl.K + C - 1) / C;
+    const R *in_arr = P::in_arr(args);
+
+    // ---- 2. thread fold (input records staged through shared memory)
     Elem agg;
-    if (start < end) {
-        SegCursor cur = P::cursor(args, start);
-        P::build(args, start, cur, agg);
-        for (int64_t p = start + 1; p < end; ++p) {
-            Elem e, t;
-            P::build(args, p, cur, e);
-            P::combine(agg, e, t);
-            agg = t;
+    {
+        bool have = false;
+        SegCursor cur = P::cursor(args, start < total ? start : total - 1);
+        if constexpr (P::IN_REC > 0) {
+            stage_load<C, P::IN_REC>(in_arr, seg_first<P, C>(total, start), total, in0, lane);
+            cp_async_commit();
         }
-    } else {
-        set_identity(agg);
+        for (int ch = 0; ch < nchunks; ++ch) {
+            if constexpr (P::IN_REC > 0) {
+                if (ch + 1 < nchunks) {
+                    stage_load<C, P::IN_REC>(in_arr, seg_first<P, C>(total, start + (ch + 1) * C), total,
+                                             ((ch + 1) & 1) ? in1 : in0, lane);
+                    cp_async_commit();
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncwarp();
+            }
+#pragma unroll 1
+            for (int c = 0; c < C; ++c) {
+                const int64_t p = start + ch * C + c;
+                if (p >= end) break;
+                const R *in = P::IN_REC ? stage_rec<C, P::IN_REC, R>((ch & 1) ? in1 : in0, lane, seg_slot<P, C>(c)) : nullptr;
+                if (!have) {
+                    P::build(args, p, cur, in, agg);
+                    have = true;
+                } else {
+                    Elem e, t;
+                    P::build(args, p, cur, in, e);
+                    P::combine(agg, e, t);
+                    agg = t;
+                }
+            }
+            __syncwarp();
+        }
+        if (!have) set_identity(agg);
     }
 
     // ---- 3. warp scan, warp-aggregate scan
@@ -304,12 +351,49 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
     }
     if (lane > 0) P::apply(c, lex);
     double ll = 0.0;
-    if (start < end) {
-        SegCursor cur = P::cursor(args, start);
-        for (int64_t p = start; p < end; ++p) {
-            Elem e;
-            P::build(args, p, cur, e);
-            ll += P::step(args, p, cur, c, e);
+    {
+        SegCursor cur = P::cursor(args, start < total ? start : total - 1);
+        R *oarr[3] = {P::out_arr(args, 0), P::out_arr(args, 1), P::out_arr(args, 2)};
+        void *obuf[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) obuf[i] = (ctl.sm_out[i] >= 0 && oarr[i]) ? wsm + ctl.sm_out[i] : nullptr;
+        // this lane's own global record range, for the stores
+        const int64_t lo = P::REV ? total - end : start, hi = P::REV ? total - start : end;
+        if constexpr (P::IN_REC > 0) {
+            stage_load<C, P::IN_REC>(in_arr, seg_first<P, C>(total, start), total, in0, lane);
+            cp_async_commit();
+        }
+        for (int ch = 0; ch < nchunks; ++ch) {
+            if constexpr (P::IN_REC > 0) {
+                if (ch + 1 < nchunks) {
+                    stage_load<C, P::IN_REC>(in_arr, seg_first<P, C>(total, start + (ch + 1) * C), total,
+                                             ((ch + 1) & 1) ? in1 : in0, lane);
+                    cp_async_commit();
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncwarp();
+            }
+#pragma unroll 1
+            for (int cc = 0; cc < C; ++cc) {
+                const int64_t p = start + ch * C + cc;
+                if (p >= end) break;
+                const int slot = seg_slot<P, C>(cc);
+                const R *in = P::IN_REC ? stage_rec<C, P::IN_REC, R>((ch & 1) ? in1 : in0, lane, slot) : nullptr;
+                R *o1 = obuf[0] ? stage_rec<C, (P::O1 ? P::O1 : 1), R>(obuf[0], lane, slot) : nullptr;
+                R *o2 = obuf[1] ? stage_rec<C, (P::O2 ? P::O2 : 1), R>(obuf[1], lane, slot) : nullptr;
+                R *o3 = obuf[2] ? stage_rec<C, (P::O3 ? P::O3 : 1), R>(obuf[2], lane, slot) : nullptr;
+                Elem e;
+                P::build(args, p, cur, in, e);
+                ll += P::step(args, p, cur, c, e, in, o1, o2, o3);
+            }
+            __syncwarp();
+            const int64_t gs = seg_first<P, C>(total, start + ch * C);
+            if constexpr (P::O1 > 0) if (obuf[0]) stage_store<C, P::O1>(oarr[0], gs, lo, hi, obuf[0], lane);
+            if constexpr (P::O2 > 0) if (obuf[1]) stage_store<C, P::O2>(oarr[1], gs, lo, hi, obuf[1], lane);
+            if constexpr (P::O3 > 0) if (obuf[2]) stage_store<C, P::O3>(oarr[2], gs, lo, hi, obuf[2], lane);
+            __syncwarp();
         }
     }
 

@@ -40,7 +40,7 @@ __global__ void lv_build(const __grid_constant__ typename P::Args args, typename
         Elem e;
         if (i < total) {
             SegCursor cur = P::cursor(args, i);
-            P::build(args, i, cur, e);
+            P::build(args, i, cur, in_rec_direct<P>(args, global_index<P>(args, i)), e);
         } else {
             set_identity(e);
         }
@@ -154,6 +154,10 @@ __global__ void __launch_bounds__(THREADS) lv_extract(const __grid_constant__ ty
     double ll = 0.0;
     for (int64_t p = gtid(); p < total; p += gstride()) {
         SegCursor cur = P::cursor(args, p);
+        const int64_t g = global_index<P>(args, p);
+        const typename P::R *in = in_rec_direct<P>(args, g);
+        typename P::R *o1 = out_rec_direct<P>(args, 0, g), *o2 = out_rec_direct<P>(args, 1, g),
+                      *o3 = out_rec_direct<P>(args, 2, g);
         if (ll_out) {
             Carry c;
             set_zero(c);
@@ -163,14 +167,14 @@ __global__ void __launch_bounds__(THREADS) lv_extract(const __grid_constant__ ty
                 P::carry_of(s, c);
             }
             Elem e;
-            P::build(args, p, cur, e);
-            ll += P::step(args, p, cur, c, e);
+            P::build(args, p, cur, in, e);
+            ll += P::step(args, p, cur, c, e, in, o1, o2, o3);
         } else {
             Elem s;
             Carry c;
             load_soa(s, a, Tpad, p);
             P::carry_of(s, c);
-            P::emit(args, p, c);
+            P::emit(args, c, in, o1, o2, o3);
         }
     }
     if (!ll_out) return;
