@@ -142,13 +142,20 @@ kf_status_t kf_sync_status(void *stream);
  *   KF_OPT_POSITIONS_PER_THREAD time steps folded serially by one thread in
  *                               the decoupled look-back scan (0 = planner's
  *                               choice: one wave of resident CTAs).
- *   KF_OPT_THREADS              CTA size of that scan: 0 (default) or 128.
+ *   KF_OPT_THREADS              CTA size of that scan: 0 (default, 128) or 128;
+ *                               256 is also built for nx = 4 in FP32.
+ *   KF_OPT_GENERAL_SOLVE        1: always invert (I + C_i J_j) of Lemma 1 by
+ *                               pivoted Gauss-Jordan; 0 (default): when
+ *                               ny = nx / 2, the filter scan's thread fold and
+ *                               carry pass use the rank-ny form of a fresh
+ *                               element's J (Woodbury identity).
  * Returns KF_ERR_ARG for an unknown option or a value out of range. */
 typedef enum {
     KF_OPT_WAIT_TIMEOUT_NS = 0,
     KF_OPT_TEST_SKIP_TILE = 1,
     KF_OPT_POSITIONS_PER_THREAD = 2,
-    KF_OPT_THREADS = 3
+    KF_OPT_THREADS = 3,
+    KF_OPT_GENERAL_SOLVE = 4
 } kf_option_t;
 kf_status_t kf_set_option(kf_option_t opt, int64_t value);
 int64_t kf_get_option(kf_option_t opt); /* -1 for an unknown option */

@@ -141,6 +141,18 @@ static kf_status_t precompute(const kf_model_t *md, HostModel *h) {
     symmetrize(m, S);
     double logdetS;
     if (!spd_inv(m, S, h->Sinv, &logdetS)) return KF_ERR_NOT_PD;
+    {   // S = L L^T, Linv = L^{-1}, U = Linv H F  (so that J = U^T U)
+        double Ls[KF_MAXM * KF_MAXM], HFt[KF_MAXM * KF_MAXN];
+        if (!chol(m, S, Ls)) return KF_ERR_NOT_PD;
+        for (int c = 0; c < m; ++c)
+            for (int i = 0; i < m; ++i) {
+                double s = (i == c) ? 1.0 : 0.0;
+                for (int k = c; k < i; ++k) s -= Ls[i * m + k] * h->Linv[k * m + c];
+                h->Linv[i * m + c] = (i < c) ? 0.0 : s / Ls[i * m + i];
+            }
+        mm(m, n, n, H, F, HFt);
+        mm(m, m, n, h->Linv, HFt, h->U);
+    }
     mm(n, m, m, QHt, h->Sinv, h->K);
     // A = (I - K H) F, C = (I - K H) Q
     double IKH[KF_MAXN * KF_MAXN];
@@ -376,6 +388,7 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
     q.inject_skip_tile = int(g_opt[KF_OPT_TEST_SKIP_TILE].load());
     q.k_override = int(g_opt[KF_OPT_POSITIONS_PER_THREAD].load());
     q.threads = int(g_opt[KF_OPT_THREADS].load());
+    q.no_lowrank = int(g_opt[KF_OPT_GENERAL_SOLVE].load());
     s = device_status_word(&q.status);
     KF_DBG("status word %p (%d)\n", (void *)q.status, int(s));
     if (s != KF_OK) return s;
@@ -536,16 +549,17 @@ kf_status_t kf_measure_fma_peak(int fp64, double *flops_per_second) {
 }
 
 kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_THREADS) return KF_ERR_ARG;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_GENERAL_SOLVE) return KF_ERR_ARG;
+    if (opt == KF_OPT_GENERAL_SOLVE && value != 0 && value != 1) return KF_ERR_ARG;
     if (opt == KF_OPT_WAIT_TIMEOUT_NS && (value < 1000000 || value > 60000000000LL)) return KF_ERR_ARG;
     if (opt == KF_OPT_POSITIONS_PER_THREAD && (value < 0 || value > (1 << 24))) return KF_ERR_ARG;
-    if (opt == KF_OPT_THREADS && value != 0 && value != 128) return KF_ERR_ARG;
+    if (opt == KF_OPT_THREADS && value != 0 && value != 128 && value != 256) return KF_ERR_ARG;
     g_opt[opt].store(value);
     return KF_OK;
 }
 
 int64_t kf_get_option(kf_option_t opt) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_THREADS) return -1;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_GENERAL_SOLVE) return -1;
     return g_opt[opt].load();
 }
 

@@ -35,6 +35,7 @@ struct HostModel {
     double HF[KF_MAXM * KF_MAXN], Sinv[KF_MAXM * KF_MAXM], S1inv[KF_MAXM * KF_MAXM], Hx1[KF_MAXM];
     double llc, llc1;
     double F[KF_MAXN * KF_MAXN], Q[KF_MAXN * KF_MAXN];
+    double U[KF_MAXM * KF_MAXN], Linv[KF_MAXM * KF_MAXM];   // J = U^T U, U = L^{-1} H F, S = L L^T
 };
 
 struct LaunchReq {
@@ -51,6 +52,7 @@ struct LaunchReq {
     int inject_skip_tile;
     int k_override;      // positions per thread (0: planner's choice)
     int threads;         // CTA size of the decoupled look-back scan (0: default)
+    int no_lowrank;      // 1: use the general Lemma 1 solve even when ny = nx / 2
 };
 
 bool debug_on();   // KFSCAN_DEBUG set in the environment

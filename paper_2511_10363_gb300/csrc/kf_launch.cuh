@@ -43,6 +43,10 @@ void to_params(const HostModel &h, FiltParams<N, R> &p) {
     }
     p.llc = h.llc;
     p.llc1 = h.llc1;
+    for (int j = 0; j < h.m; ++j) {
+        for (int k = 0; k < n; ++k) p.U[j * N + k] = R(h.U[j * n + k]);
+        for (int k = 0; k < h.m; ++k) p.Linv[j * MAXNY + k] = R(h.Linv[j * h.m + k]);
+    }
     p.ny = h.m;
 }
 
@@ -312,7 +316,15 @@ static cudaError_t launch_typed(const LaunchReq &q) {
     fa.src.T = q.T;
     fa.buf = buf;
     fa.want_ll = q.loglik != nullptr;
-    cudaError_t e = run_scan<FilterFwd<N, R, MODE, Src>, THREADS, V>(fa, ws, L.ctl_f, L, q, q.loglik);
+    cudaError_t e;
+    constexpr int LRM = N / 2;   // low-rank filter path when ny = nx / 2
+    if (q.hm->m == LRM && q.scan == KF_SCAN_DLB_I && !q.no_lowrank) {
+        typename FilterFwd<N, R, MODE, Src, LRM>::Args fl;
+        memcpy(&fl, &fa, sizeof(fl));
+        e = run_scan<FilterFwd<N, R, MODE, Src, LRM>, THREADS, V>(fl, ws, L.ctl_f, L, q, q.loglik);
+    } else {
+        e = run_scan<FilterFwd<N, R, MODE, Src>, THREADS, V>(fa, ws, L.ctl_f, L, q, q.loglik);
+    }
     if (e != cudaSuccess || q.op == KF_OP_FILTER_I) return e;
     if (q.op == KF_OP_RTS_I) {
         typename RtsRev<N, R, Src>::Args ra;

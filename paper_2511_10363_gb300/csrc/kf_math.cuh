@@ -110,10 +110,16 @@ struct FiltParams {
     R Hx1[MAXNY];                 //   H xbar_{1|0}
     double llc, llc1;             //   log det S + m log 2 pi,  log det S_1 + m log 2 pi
     R F[NN], Q[S];                // RTS elements, Eq. prts_init1
+    R U[MAXNY * N];               // J = U^T U, U = L^{-1} H F with S = L L^T (low-rank path)
+    R Linv[MAXNY * MAXNY];        //   L^{-1} (lower triangular)
     int ny;
 };
 
 // ---------------------------------------------------------------- small solves
+
+// Correctly rounded reciprocal (the CUDA intrinsic for FP32).
+KF_D float recip(float x) { return __frcp_rn(x); }
+KF_D double recip(double x) { return __drcp_rn(x); }
 
 // X = (I + C J)^{-1} for packed symmetric C, J, by Gauss-Jordan elimination
 // with partial pivoting in precision T.  Returns sum log|pivot| = log det(I + C J)
@@ -158,7 +164,7 @@ KF_D void inv_I_plus_CJ_T(const RC *C, const RJ *J, T X[N * N], T &logdet) {
         }
         const T piv = a[c * N + c];
         if (LD) logdet += log(fabs(piv));
-        const T d = T(1) / piv;
+        const T d = recip(piv);
 #pragma unroll
         for (int j = c + 1; j < N; ++j) a[c * N + j] *= d;
 #pragma unroll
@@ -521,6 +527,404 @@ KF_D void apply_rev(RevCarry<N, R> &c, const FElem<N, R> &ei) {
 #pragma unroll
             for (int k = 0; k < N; ++k) s += Z[k * N + r] * W[k * N + q];
             c.v[CT::oJ + su(N, r, q)] = s;
+        }
+}
+
+
+// ---------------------------------------------------------------- low-rank path
+//
+// For a fresh filtering element a_k the information matrix has rank m:
+// J_k = F^T H^T S^{-1} H F = U^T U with U = L^{-1} H F (m x n), S = L L^T.
+// By the Woodbury identity
+//     (I + C U^T U)^{-1} = I - C U^T W U,   W = (I_m + U C U^T)^{-1},
+// where I_m + U C U^T is m x m symmetric positive definite with eigenvalues
+// >= 1, so W needs no pivoting; with G = U C (so C U^T = G^T):
+//     X C   = C - G^T W G               (symmetric)
+//     X A   = A - G^T W (U A)
+//     X v   = v - G^T W (U v)
+// and, by Sylvester's determinant identity, det(I + C J_k) = det(I_m + U C U^T).
+
+// Inverse and log-determinant of a small SPD matrix given by its packed
+// upper triangle (M = 1, 2 closed forms; larger M by Cholesky).
+template <int M, typename T>
+KF_D void spd_inverse(const T *Pp, T *W, T &logdet) {
+    if constexpr (M == 1) {
+        W[0] = recip(Pp[0]);
+        logdet = log(Pp[0]);
+    } else if constexpr (M == 2) {
+        const T det = Pp[0] * Pp[2] - Pp[1] * Pp[1];
+        const T r = recip(det);
+        W[0] = Pp[2] * r;
+        W[1] = -Pp[1] * r;
+        W[2] = Pp[0] * r;
+        logdet = log(det);
+    } else {
+        T L[M * (M + 1) / 2], dinv[M];
+        T ld = 0;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) {
+                T s = Pp[su(M, j, i)];
+#pragma unroll
+                for (int k = 0; k < j; ++k) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+                if (i == j) {
+                    const T d = sqrt(s);
+                    L[i * (i + 1) / 2 + i] = d;
+                    dinv[i] = recip(d);
+                    ld += log(s);
+                } else {
+                    L[i * (i + 1) / 2 + j] = s * dinv[j];
+                }
+            }
+        // Linv (lower), then W = Linv^T Linv
+        T Li[M * M];
+#pragma unroll
+        for (int c = 0; c < M; ++c)
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                if (i < c) {
+                    Li[i * M + c] = 0;
+                    continue;
+                }
+                T s = (i == c) ? T(1) : T(0);
+#pragma unroll
+                for (int k = 0; k < i; ++k)
+                    if (k >= c) s -= L[i * (i + 1) / 2 + k] * Li[k * M + c];
+                Li[i * M + c] = s * dinv[i];
+            }
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+            for (int j = i; j < M; ++j) {
+                T s = 0;
+#pragma unroll
+                for (int k = 0; k < M; ++k) s += Li[k * M + i] * Li[k * M + j];
+                W[su(M, i, j)] = s;
+            }
+        logdet = ld;
+    }
+}
+
+// G = U C (M x N), W = (I_M + G U^T)^{-1} (packed M x M) and log det of it.
+// MODE 1 forms I + G U^T and inverts it in FP64, then applies one step of
+// iterative refinement W <- W + W (I - P W) in FP64.
+template <int N, int M, typename R, int MODE>
+KF_D void lowrank_core(const R *C, const R *U, R G[M * N], R Wp[M * (M + 1) / 2], double &logdet) {
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += U[i * N + k] * C[si(N, k, c)];
+            G[i * N + c] = s;
+        }
+    if constexpr (MODE == 0) {
+        R Pp[M * (M + 1) / 2];
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+            for (int j = i; j < M; ++j) {
+                R s = (i == j) ? R(1) : R(0);
+#pragma unroll
+                for (int k = 0; k < N; ++k) s += G[i * N + k] * U[j * N + k];
+                Pp[su(M, i, j)] = s;
+            }
+        R ld;
+        spd_inverse<M, R>(Pp, Wp, ld);
+        logdet = double(ld);
+    } else {
+        double Pp[M * (M + 1) / 2], Wd[M * (M + 1) / 2];
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+            for (int j = i; j < M; ++j) {
+                double s = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+                for (int k = 0; k < N; ++k) s += double(G[i * N + k]) * double(U[j * N + k]);
+                Pp[su(M, i, j)] = s;
+            }
+        double ld;
+        spd_inverse<M, double>(Pp, Wd, ld);
+        // refinement: E = I - P W, W <- W + W E (symmetric result)
+        double E[M * M];
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                double t = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+                for (int k = 0; k < M; ++k) t -= Pp[si(M, i, k)] * Wd[si(M, k, j)];
+                E[i * M + j] = t;
+            }
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+            for (int j = i; j < M; ++j) {
+                double t = Wd[su(M, i, j)];
+#pragma unroll
+                for (int k = 0; k < M; ++k) t += Wd[si(M, i, k)] * E[k * M + j];
+                Wp[su(M, i, j)] = R(t);
+            }
+        logdet = ld;
+    }
+}
+
+// Lemma 1, ei (x) ej, for a fresh right operand ej whose J is U^T U.
+template <int N, int M, typename R, int MODE>
+KF_D void lemma1_lr(const FElem<N, R> &ei, const FElem<N, R> &ej, const R *U, FElem<N, R> &o) {
+    using E = FElem<N, R>;
+    constexpr int SM = M * (M + 1) / 2;
+    const R *Ai = ei.v + E::oA, *bi = ei.v + E::ob, *Ci = ei.v + E::oC, *etai = ei.v + E::oe, *Ji = ei.v + E::oJ;
+    const R *Aj = ej.v + E::oA, *bj = ej.v + E::ob, *Cj = ej.v + E::oC, *etaj = ej.v + E::oe;
+    R G[M * N], W[SM];
+    double ld;
+    lowrank_core<N, M, R, MODE>(Ci, U, G, W, ld);
+    // WG = W G; D = C_i - G^T W G
+    R WG[M * N];
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < M; ++k) s += W[si(M, i, k)] * G[k * N + c];
+            WG[i * N + c] = s;
+        }
+    R D[N * (N + 1) / 2];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = r; c < N; ++c) {
+            R s = Ci[su(N, r, c)];
+#pragma unroll
+            for (int k = 0; k < M; ++k) s -= G[k * N + r] * WG[k * N + c];
+            D[su(N, r, c)] = s;
+        }
+    // UA = U A_i, WUA = W UA, Z = A_i - G^T WUA  (= X A_i)
+    R UA[M * N], WUA[M * N];
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += U[i * N + k] * Ai[k * N + c];
+            UA[i * N + c] = s;
+        }
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < M; ++k) s += W[si(M, i, k)] * UA[k * N + c];
+            WUA[i * N + c] = s;
+        }
+    R Z[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = Ai[r * N + c];
+#pragma unroll
+            for (int k = 0; k < M; ++k) s -= G[k * N + r] * WUA[k * N + c];
+            Z[r * N + c] = s;
+        }
+    // Ub = U b_i; u = b_i - G^T W Ub + D eta_j  (= X (b_i + C_i eta_j))
+    R Ub[M], WUb[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        R s = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += U[i * N + k] * bi[k];
+        Ub[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        R s = 0;
+#pragma unroll
+        for (int k = 0; k < M; ++k) s += W[si(M, i, k)] * Ub[k];
+        WUb[i] = s;
+    }
+    R u[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = bi[r];
+#pragma unroll
+        for (int k = 0; k < M; ++k) s -= G[k * N + r] * WUb[k];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += D[si(N, r, k)] * etaj[k];
+        u[r] = s;
+    }
+    // w = eta_j - U^T Ub  (= eta_j - J_j b_i);  Wj = U^T UA  (= J_j A_i)
+    R w[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = etaj[r];
+#pragma unroll
+        for (int k = 0; k < M; ++k) s -= U[k * N + r] * Ub[k];
+        w[r] = s;
+    }
+    R AD[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Aj[r * N + k] * D[si(N, k, c)];
+            AD[r * N + c] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Aj[r * N + k] * Z[k * N + c];
+            o.v[E::oA + r * N + c] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = bj[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += Aj[r * N + k] * u[k];
+        o.v[E::ob + r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = r; c < N; ++c) {
+            R s = Cj[su(N, r, c)];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += AD[r * N + k] * Aj[c * N + k];
+            o.v[E::oC + su(N, r, c)] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = etai[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += Z[k * N + r] * w[k];
+        o.v[E::oe + r] = s;
+    }
+    R Wj[N * N];
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R s = 0;
+#pragma unroll
+            for (int q = 0; q < M; ++q) s += U[q * N + k] * UA[q * N + c];
+            Wj[k * N + c] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = r; c < N; ++c) {
+            R s = Ji[su(N, r, c)];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Z[k * N + r] * Wj[k * N + c];
+            o.v[E::oJ + su(N, r, c)] = s;
+        }
+}
+
+// (b, C) half of Lemma 1 for a fresh right operand: c <- c (x) ej.  With LL
+// it also returns, for ytil = L^{-1} y_k, the whitened innovation
+// vt = ytil - U b (before the update) and vt^T W vt and log det(I_m + U C U^T),
+// which give log N(y_k; H F b, S_k) since S_k = L (I_m + U C U^T) L^T.
+template <int N, int M, typename R, int MODE, bool LL>
+KF_D void apply_fwd_lr(FwdCarry<N, R> &c, const FElem<N, R> &ej, const R *U, const R *ytil, R *quad,
+                       double *logdet) {
+    using E = FElem<N, R>;
+    using CT = FwdCarry<N, R>;
+    const R *b = c.v + CT::ob, *C = c.v + CT::oC;
+    const R *Aj = ej.v + E::oA, *bj = ej.v + E::ob, *Cj = ej.v + E::oC, *etaj = ej.v + E::oe;
+    R G[M * N], W[M * (M + 1) / 2];
+    double ld;
+    lowrank_core<N, M, R, MODE>(C, U, G, W, ld);
+    R WG[M * N];
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < M; ++k) s += W[si(M, i, k)] * G[k * N + q];
+            WG[i * N + q] = s;
+        }
+    R D[N * (N + 1) / 2];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int q = r; q < N; ++q) {
+            R s = C[su(N, r, q)];
+#pragma unroll
+            for (int k = 0; k < M; ++k) s -= G[k * N + r] * WG[k * N + q];
+            D[su(N, r, q)] = s;
+        }
+    R Ub[M], WUb[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        R s = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += U[i * N + k] * b[k];
+        Ub[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        R s = 0;
+#pragma unroll
+        for (int k = 0; k < M; ++k) s += W[si(M, i, k)] * Ub[k];
+        WUb[i] = s;
+    }
+    if constexpr (LL) {
+        R vt[M], q = 0;
+#pragma unroll
+        for (int i = 0; i < M; ++i) vt[i] = ytil[i] - Ub[i];
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+            for (int k = 0; k < M; ++k) q += vt[i] * W[si(M, i, k)] * vt[k];
+        *quad = q;
+        *logdet = ld;
+    }
+    R u[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = b[r];
+#pragma unroll
+        for (int k = 0; k < M; ++k) s -= G[k * N + r] * WUb[k];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += D[si(N, r, k)] * etaj[k];
+        u[r] = s;
+    }
+    R AD[N * N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += Aj[r * N + k] * D[si(N, k, q)];
+            AD[r * N + q] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R s = bj[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += Aj[r * N + k] * u[k];
+        c.v[CT::ob + r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int q = r; q < N; ++q) {
+            R s = Cj[su(N, r, q)];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s += AD[r * N + k] * Aj[q * N + k];
+            c.v[CT::oC + su(N, r, q)] = s;
         }
 }
 

@@ -5,6 +5,9 @@ namespace kfs {
 
 size_t ws_bytes_n4_f32(int op, int scan, int64_t T) { return ws_layout<4, float>(op, scan, T).total; }
 
-cudaError_t launch_n4_f32(const LaunchReq &q) { return launch_typed<4, float, 0, 128>(q); }
+cudaError_t launch_n4_f32(const LaunchReq &q) {
+    if (q.threads == 256) return launch_typed<4, float, 0, 256>(q);
+    return launch_typed<4, float, 0, 128>(q);
+}
 
 }  // namespace kfs

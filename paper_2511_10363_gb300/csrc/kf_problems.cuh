@@ -126,6 +126,24 @@ template <int N, typename R, int MODE, bool LL>
 KF_D void op_apply_fwd(FwdCarry<N, R> &c, const FElem<N, R> &e, double *ld, R *q) {
     if constexpr (N >= 8) apply_fwd_ool<N, R, MODE, LL>(c, e, ld, q); else apply_fwd<N, R, MODE, LL>(c, e, ld, q);
 }
+template <int N, int M, typename R, int MODE>
+__device__ __noinline__ void lemma1_lr_ool(const FElem<N, R> &a, const FElem<N, R> &b, const R *U, FElem<N, R> &o) {
+    lemma1_lr<N, M, R, MODE>(a, b, U, o);
+}
+template <int N, int M, typename R, int MODE>
+KF_D void op_lemma1_lr(const FElem<N, R> &a, const FElem<N, R> &b, const R *U, FElem<N, R> &o) {
+    if constexpr (N >= 8) lemma1_lr_ool<N, M, R, MODE>(a, b, U, o); else lemma1_lr<N, M, R, MODE>(a, b, U, o);
+}
+template <int N, int M, typename R, int MODE, bool LL>
+__device__ __noinline__ void apply_fwd_lr_ool(FwdCarry<N, R> &c, const FElem<N, R> &e, const R *U, const R *yt, R *q,
+                                              double *ld) {
+    apply_fwd_lr<N, M, R, MODE, LL>(c, e, U, yt, q, ld);
+}
+template <int N, int M, typename R, int MODE, bool LL>
+KF_D void op_apply_fwd_lr(FwdCarry<N, R> &c, const FElem<N, R> &e, const R *U, const R *yt, R *q, double *ld) {
+    if constexpr (N >= 8) apply_fwd_lr_ool<N, M, R, MODE, LL>(c, e, U, yt, q, ld);
+    else apply_fwd_lr<N, M, R, MODE, LL>(c, e, U, yt, q, ld);
+}
 template <int N, typename R, int MODE>
 __device__ __noinline__ void apply_rev_ool(RevCarry<N, R> &c, const FElem<N, R> &e) { apply_rev<N, R, MODE>(c, e); }
 template <int N, typename R, int MODE>
@@ -171,7 +189,9 @@ KF_D void op_tf_merge(const R *x, const R *Pk, const RevCarry<N, R> &c, R *ms, R
 // pointers, which point either into a warp's shared-memory staging buffer or
 // straight into device memory.
 
-template <int N, typename Rt, int MODE, class Src>
+// LR > 0: every fresh element's J is U^T U of rank LR = ny, and the thread
+// fold and the carry pass use the low-rank forms (kf_math.cuh).
+template <int N, typename Rt, int MODE, class Src, int LR = 0>
 struct FilterFwd {
     static constexpr int KIND = 0;
     static constexpr bool REV = false;
@@ -195,7 +215,18 @@ struct FilterFwd {
         build_filter_elem<N, R>(P, p - cur.b + 1, a.buf.y + p * P.ny, e);
     }
     static KF_D void combine(const Elem &x, const Elem &y, Elem &o) { op_lemma1<N, R, MODE>(x, y, o); }
+    // x (x) y where y is the element of position p (fresh)
+    static KF_D void fold(const Args &a, const SegCursor &cur, const Elem &x, const Elem &y, Elem &o) {
+        if constexpr (LR > 0) op_lemma1_lr<N, LR, R, MODE>(x, y, seg_params(a.src, cur).U, o);
+        else op_lemma1<N, R, MODE>(x, y, o);
+    }
     static KF_D void apply(Carry &c, const Elem &e) { op_apply_fwd<N, R, MODE, false>(c, e, nullptr, nullptr); }
+    static KF_D void apply_fresh(const Args &a, const SegCursor &cur, Carry &c, const Elem &e) {
+        if constexpr (LR > 0)
+            op_apply_fwd_lr<N, LR, R, MODE, false>(c, e, seg_params(a.src, cur).U, nullptr, nullptr, nullptr);
+        else
+            op_apply_fwd<N, R, MODE, false>(c, e, nullptr, nullptr);
+    }
     static KF_D void carry_of(const Elem &e, Carry &c) {
 #pragma unroll
         for (int i = 0; i < N; ++i) c.v[Carry::ob + i] = e.v[Elem::ob + i];
@@ -224,7 +255,7 @@ struct FilterFwd {
     static KF_D double step(const Args &a, int64_t p, SegCursor &cur, Carry &c, const Elem &e, const R *in, R *o1,
                             R *o2, R *o3) {
         if (!a.want_ll) {
-            apply(c, e);
+            apply_fresh(a, cur, c, e);
             emit(a, c, in, o1, o2, o3);
             return 0.0;
         }
@@ -243,7 +274,20 @@ struct FilterFwd {
                 for (int j = 0; j < MAXNY; ++j)
                     if (i < ny && j < ny) q += v[i] * P.S1inv[i * MAXNY + j] * v[j];
             ll = -0.5 * (double(q) + P.llc1);
-            apply(c, e);
+            apply_fresh(a, cur, c, e);
+        } else if constexpr (LR > 0) {
+            R yt[LR];
+#pragma unroll
+            for (int i = 0; i < LR; ++i) {
+                R s = 0;
+#pragma unroll
+                for (int k = 0; k <= i; ++k) s += P.Linv[i * MAXNY + k] * yk[k];
+                yt[i] = s;
+            }
+            R q;
+            double ld;
+            op_apply_fwd_lr<N, LR, R, MODE, true>(c, e, P.U, yt, &q, &ld);
+            ll = -0.5 * (double(q) + ld + P.llc);
         } else {
             const R *b = c.v + Carry::ob;
             R v[MAXNY];
@@ -303,6 +347,7 @@ struct TfRev {
         build_filter_elem<N, R>(P, g - cur.b + 2, a.buf.y + (g + 1) * P.ny, e);
     }
     static KF_D void combine(const Elem &x, const Elem &y, Elem &o) { op_lemma1<N, R, MODE>(y, x, o); }
+    static KF_D void fold(const Args &, const SegCursor &, const Elem &x, const Elem &y, Elem &o) { combine(x, y, o); }
     static KF_D void apply(Carry &c, const Elem &e) { op_apply_rev<N, R, MODE>(c, e); }
     static KF_D void carry_of(const Elem &e, Carry &c) {
 #pragma unroll
@@ -362,6 +407,7 @@ struct RtsRev {
         op_build_rts<N, R>(P, g == cur.e - 1, x, Pk, e);
     }
     static KF_D void combine(const Elem &x, const Elem &y, Elem &o) { op_lemma2<N, R>(y, x, o); }
+    static KF_D void fold(const Args &, const SegCursor &, const Elem &x, const Elem &y, Elem &o) { combine(x, y, o); }
     static KF_D void apply(Carry &c, const Elem &e) { op_apply_rts<N, R>(c, e); }
     static KF_D void carry_of(const Elem &e, Carry &c) {
 #pragma unroll

@@ -18,7 +18,8 @@
 //      element at a time with the one-sided operator, and emits its outputs
 //      (extraction fused into the scan).
 // The launcher keeps the number of tiles <= THREADS * V, so one look-back
-// window always covers every predecessor.
+// window (ceil(ntiles / THREADS) predecessors per thread) always covers every
+// predecessor.
 //
 // Every wait is bounded by a wall-clock limit (%globaltimer); on time-out the
 // CTA records KF_ERR_TIMEOUT in the status word and returns; other CTAs see
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
                 } else {
                     Elem e, t;
                     P::build(args, p, cur, in, e);
-                    P::combine(agg, e, t);
+                    P::fold(args, cur, agg, e, t);
                     agg = t;
                 }
             }
@@ -186,8 +187,8 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
         if (!have) set_identity(agg);
     }
 
-    // ---- 3. warp scan, warp-aggregate scan
-#pragma unroll
+    // ---- 3. warp scan, warp-aggregate scan (cold: kept rolled for code size)
+#pragma unroll 1
     for (int s = 1; s < 32; s <<= 1) {
         Elem o, t;
         shfl_up_x(agg, o, s);
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
         } else {
             set_identity(w);
         }
-#pragma unroll
+#pragma unroll 1
         for (int s = 1; s < NW; s <<= 1) {
             Elem o, t;
             shfl_up_x(w, o, s);
@@ -251,16 +252,16 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
     Carry tc;
     set_zero(tc);
     if (tile > 0) {
-        int fl[V];
+        // predecessors q = tile-1-(tid*vv + v), v < vv; vv*THREADS >= ntiles
+        const int vv = (ctl.ntiles + THREADS - 1) / THREADS;
         int qloc = -1;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const int q = tile - 1 - (tid * V + v);
-            fl[v] = 0;
+#pragma unroll 1
+        for (int v = 0; v < vv; ++v) {
+            const int q = tile - 1 - (tid * vv + v);
             if (q >= 0) {
-                fl[v] = wait_flag(ctl.flags + q, ctl);
-                if (fl[v] == 0) s_abort = 1;
-                if (fl[v] == 2 && q > qloc) qloc = q;
+                const int f = wait_flag(ctl.flags + q, ctl);
+                if (f == 0) s_abort = 1;
+                if (f == 2 && q > qloc) qloc = q;
             }
         }
         if (qloc >= 0) atomicMax(&s_qstar, qloc);
@@ -270,9 +271,9 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
         // fold the aggregates of my predecessors after qstar, earliest first
         Elem x;
         bool have = false;
-#pragma unroll
-        for (int v = V - 1; v >= 0; --v) {
-            const int q = tile - 1 - (tid * V + v);
+#pragma unroll 1
+        for (int v = vv - 1; v >= 0; --v) {
+            const int q = tile - 1 - (tid * vv + v);
             if (q > qstar) {
                 Elem a;
                 load_cg(a, static_cast<const R *>(ctl.agg) + int64_t(q) * ES);
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
         }
         if (!have) set_identity(x);
         // lane l covers later tiles than lane l+1: suffix reduction to lane 0
-#pragma unroll
+#pragma unroll 1
         for (int s = 1; s < 32; s <<= 1) {
             Elem o, t;
             shfl_down_x(x, o, s);
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
             } else {
                 set_identity(y);
             }
-#pragma unroll
+#pragma unroll 1
             for (int s = 1; s < NW; s <<= 1) {
                 Elem o, t;
                 shfl_down_x(y, o, s);

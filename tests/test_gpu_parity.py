@@ -113,3 +113,21 @@ def test_deterministic_loglik():
     l1 = gpu_run("filter", model, y, "fp64", "dlb", loglik=True)["ll"]
     l2 = gpu_run("filter", model, y, "fp64", "dlb", loglik=True)["ll"]
     assert l1 == l2
+
+
+@pytest.mark.parametrize("general", [0, 1])
+@pytest.mark.parametrize("precision", PRECS)
+@pytest.mark.parametrize("nx", [2, 4, 8])
+def test_filter_solve_forms(general, precision, nx):
+    """With ny = nx / 2 the filter scan uses the rank-ny (Woodbury) form of a
+    fresh element's J unless the general pivoted inverse is forced; both
+    must match the oracle, the log-likelihood included."""
+    import paper_2511_10363_gb300 as kf
+    model = model_for(nx, seed=41 + nx)
+    y = W.simulate(model, 3000, seed=42 + nx)
+    kf.kf_set_option("general_solve", general)
+    try:
+        for op in ("filter", "rts", "tf"):
+            compare(op, model, y, precision, "dlb")
+    finally:
+        kf.kf_set_option("general_solve", 0)
