@@ -149,13 +149,18 @@ kf_status_t kf_sync_status(void *stream);
  *                               ny = nx / 2, the filter scan's thread fold and
  *                               carry pass use the rank-ny form of a fresh
  *                               element's J (Woodbury identity).
+ *   KF_OPT_LOOKBACK_WARPS       warps of a CTA that reduce the predecessor
+ *                               aggregates in the look-back: 0 (default: the
+ *                               library's choice) or 1 .. 32 (capped at the
+ *                               CTA's warp count).
  * Returns KF_ERR_ARG for an unknown option or a value out of range. */
 typedef enum {
     KF_OPT_WAIT_TIMEOUT_NS = 0,
     KF_OPT_TEST_SKIP_TILE = 1,
     KF_OPT_POSITIONS_PER_THREAD = 2,
     KF_OPT_THREADS = 3,
-    KF_OPT_GENERAL_SOLVE = 4
+    KF_OPT_GENERAL_SOLVE = 4,
+    KF_OPT_LOOKBACK_WARPS = 5
 } kf_option_t;
 kf_status_t kf_set_option(kf_option_t opt, int64_t value);
 int64_t kf_get_option(kf_option_t opt); /* -1 for an unknown option */
@@ -179,6 +184,15 @@ typedef enum {
 kf_status_t kf_timing_enable(int on);
 kf_status_t kf_timing_reset(void);
 kf_status_t kf_timing_read(kf_kernel_t kind, int64_t *launches, double *total_ms);
+
+/* Phase trace (diagnostics).  While a buffer is set for a decoupled
+ * look-back scan kind (FILTER/RTS/TF_SCAN), every later launch of that scan
+ * writes, for each tile t < capacity_tiles, five %globaltimer stamps (ns) to
+ * device_buffer[8 t .. 8 t + 4]: CTA start, end of the thread fold + warp
+ * scan, aggregate published, look-back done, end of the extraction pass.
+ * device_buffer is a caller-owned DEVICE buffer of 8 * capacity_tiles
+ * uint64; NULL switches the trace off. */
+kf_status_t kf_trace_phases(kf_kernel_t kind, void *device_buffer, int capacity_tiles);
 
 /* Measures the FP32 (fp64 = 0) or FP64 (fp64 = 1) fused multiply-add
  * throughput of the current device with a kernel of independent FMA chains

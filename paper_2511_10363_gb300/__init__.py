@@ -29,7 +29,8 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_fp64solve": 2, "mixed": 2}
 OPS = {"filter": 0, "rts": 1, "two_filter": 2, "tf": 2}
 STATUS = {0: "KF_OK", 1: "KF_ERR_ARG", 2: "KF_ERR_NOT_PD", 3: "KF_ERR_CUDA", 4: "KF_ERR_OOM",
           5: "KF_ERR_TIMEOUT", 6: "KF_ERR_BUDGET", 7: "KF_ERR_BUSY"}
-OPTIONS = {"wait_timeout_ns": 0, "test_skip_tile": 1, "positions_per_thread": 2, "threads": 3, "general_solve": 4}
+OPTIONS = {"wait_timeout_ns": 0, "test_skip_tile": 1, "positions_per_thread": 2, "threads": 3, "general_solve": 4,
+           "lookback_warps": 5}
 
 _lib = None
 
@@ -75,6 +76,8 @@ def lib():
         L.kf_timing_enable.argtypes = [i]
         L.kf_timing_read.argtypes = [i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
         L.kf_measure_fma_peak.argtypes = [i, ctypes.POINTER(ctypes.c_double)]
+        L.kf_trace_phases.argtypes = [i, vp, i]
+        L.kf_trace_phases.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -252,3 +255,10 @@ def rts_smooth_host(model, y_host, precision, scan, ms_host, Ps_host, ll_host=No
     if ll_host is not None:
         ll_host.copy_(ll_dev, non_blocking=True)
     return ms_host, Ps_host, ll_host
+
+
+def kf_trace_phases(kind, buf=None):
+    """Set (or clear, buf=None) the phase-trace device buffer (int64 tensor
+    of 8 * capacity entries) of a look-back scan kind."""
+    cap = 0 if buf is None else buf.numel() // 8
+    _check(lib().kf_trace_phases(int(kind), _ptr(buf), cap), "kf_trace_phases")

@@ -243,6 +243,14 @@ static double g_tms[KF_KERNEL_KINDS];
 static int64_t g_tlaunch0[KF_KERNEL_KINDS];
 
 void count_launches(int kind, int n) { g_launches[kind] += n; }
+
+static uint64_t *g_trace[KF_KERNEL_KINDS];
+static int g_trace_cap[KF_KERNEL_KINDS];
+void trace_target(int kind, uint64_t **buf, int *cap) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    *buf = g_trace[kind];
+    *cap = g_trace_cap[kind];
+}
 bool timing_on() { return g_timing.load() != 0; }
 void timing_record(int, cudaStream_t s, cudaEvent_t *ev) {
     if (cudaEventCreate(ev) != cudaSuccess) { *ev = nullptr; return; }
@@ -389,6 +397,7 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
     q.k_override = int(g_opt[KF_OPT_POSITIONS_PER_THREAD].load());
     q.threads = int(g_opt[KF_OPT_THREADS].load());
     q.no_lowrank = int(g_opt[KF_OPT_GENERAL_SOLVE].load());
+    q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
     s = device_status_word(&q.status);
     KF_DBG("status word %p (%d)\n", (void *)q.status, int(s));
     if (s != KF_OK) return s;
@@ -519,6 +528,15 @@ kf_status_t kf_sync_status(void *stream) {
     return KF_OK;
 }
 
+kf_status_t kf_trace_phases(kf_kernel_t kind, void *device_buffer, int capacity_tiles) {
+    if (kind < 0 || kind > KF_KERNEL_TF_SCAN || capacity_tiles < 0) return KF_ERR_ARG;
+    if (device_buffer && (reinterpret_cast<uintptr_t>(device_buffer) % 8)) return KF_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_trace[kind] = static_cast<uint64_t *>(device_buffer);
+    g_trace_cap[kind] = device_buffer ? capacity_tiles : 0;
+    return KF_OK;
+}
+
 kf_status_t kf_timing_enable(int on) {
     g_timing.store(on ? 1 : 0);
     return KF_OK;
@@ -549,8 +567,9 @@ kf_status_t kf_measure_fma_peak(int fp64, double *flops_per_second) {
 }
 
 kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_GENERAL_SOLVE) return KF_ERR_ARG;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_LOOKBACK_WARPS) return KF_ERR_ARG;
     if (opt == KF_OPT_GENERAL_SOLVE && value != 0 && value != 1) return KF_ERR_ARG;
+    if (opt == KF_OPT_LOOKBACK_WARPS && (value < 0 || value > 32)) return KF_ERR_ARG;
     if (opt == KF_OPT_WAIT_TIMEOUT_NS && (value < 1000000 || value > 60000000000LL)) return KF_ERR_ARG;
     if (opt == KF_OPT_POSITIONS_PER_THREAD && (value < 0 || value > (1 << 24))) return KF_ERR_ARG;
     if (opt == KF_OPT_THREADS && value != 0 && value != 128 && value != 256) return KF_ERR_ARG;
@@ -559,7 +578,7 @@ kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
 }
 
 int64_t kf_get_option(kf_option_t opt) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_GENERAL_SOLVE) return -1;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_LOOKBACK_WARPS) return -1;
     return g_opt[opt].load();
 }
 

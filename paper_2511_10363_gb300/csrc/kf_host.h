@@ -53,6 +53,7 @@ struct LaunchReq {
     int k_override;      // positions per thread (0: planner's choice)
     int threads;         // CTA size of the decoupled look-back scan (0: default)
     int no_lowrank;      // 1: use the general Lemma 1 solve even when ny = nx / 2
+    int lookback_warps;  // warps of a CTA that take part in the look-back (0: all)
 };
 
 bool debug_on();   // KFSCAN_DEBUG set in the environment
@@ -62,6 +63,7 @@ void count_launches(int kind, int n);
 bool timing_on();
 void timing_record(int kind, cudaStream_t s, cudaEvent_t *ev);          // start event
 void timing_commit(int kind, cudaStream_t s, cudaEvent_t start);        // stop event
+void trace_target(int kind, uint64_t **buf, int *cap);                  // phase trace buffer of a scan kind
 size_t ws_bytes_dispatch(int nx, int op, int prec, int scan, int64_t T);
 cudaError_t launch_dispatch(const LaunchReq &q);
 

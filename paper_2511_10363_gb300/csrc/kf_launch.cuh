@@ -203,6 +203,10 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
     ctl.ntiles = tp.ntiles;
     ctl.K = tp.K;
     ctl.inject_skip_tile = q.inject_skip_tile;
+    ctl.lbw = (q.lookback_warps > 0 && q.lookback_warps <= THREADS / 32) ? q.lookback_warps : THREADS / 32;
+    ctl.trace = nullptr;
+    ctl.trace_cap = 0;
+    trace_target(P::KIND, &ctl.trace, &ctl.trace_cap);
     cudaError_t e = cudaMemsetAsync(ctl.counters, 0, sizeof(int) * (2 + tp.ntiles), q.stream);
     if (debug_on())
         fprintf(stderr, "[kfscan] dlb: total=%lld tiles=%d K=%d C=%d threads=%d smem=%d memset=%d\n",
@@ -301,6 +305,7 @@ static cudaError_t launch_typed(const LaunchReq &q) {
     using Src = OneSeq<N, R>;
     constexpr int V = (1024 + THREADS - 1) / THREADS;
     static_assert(THREADS * V <= KF_MAX_TILES, "look-back window larger than the flag array");
+    static_assert(THREADS <= 1024, "CTA too large");
     const WsLayout L = ws_layout<N, R>(q.op, q.scan, q.T);
     char *ws = static_cast<char *>(q.ws);
     KfBufs<R> buf;

@@ -93,6 +93,57 @@ KF_HD void set_identity(RElem<N, R> &e) {
     for (int i = 0; i < N; ++i) e.v[RElem<N, R>::oE + i * N + i] = R(1);
 }
 
+// ---------------------------------------------------------------- record copies
+
+// Copy REC consecutive values between a record (shared or device memory,
+// aligned to its size class) and registers with the widest vector accesses
+// the record allows (16-, 8- or 4-byte), so that a warp reading its lanes'
+// records from a staging buffer with an odd 16-byte stride is conflict-free.
+template <int REC, typename R>
+KF_D void load_rec(R *dst, const R *src) {
+    constexpr int B = REC * int(sizeof(R));
+    if constexpr (B % 16 == 0 && sizeof(R) == 4) {
+#pragma unroll
+        for (int i = 0; i < REC / 4; ++i) {
+            const float4 v = reinterpret_cast<const float4 *>(src)[i];
+            dst[4 * i] = v.x; dst[4 * i + 1] = v.y; dst[4 * i + 2] = v.z; dst[4 * i + 3] = v.w;
+        }
+    } else if constexpr (B % 16 == 0 && sizeof(R) == 8) {
+#pragma unroll
+        for (int i = 0; i < REC / 2; ++i) {
+            const double2 v = reinterpret_cast<const double2 *>(src)[i];
+            dst[2 * i] = v.x; dst[2 * i + 1] = v.y;
+        }
+    } else if constexpr (B % 8 == 0 && sizeof(R) == 4) {
+#pragma unroll
+        for (int i = 0; i < REC / 2; ++i) {
+            const float2 v = reinterpret_cast<const float2 *>(src)[i];
+            dst[2 * i] = v.x; dst[2 * i + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < REC; ++i) dst[i] = src[i];
+    }
+}
+template <int REC, typename R>
+KF_D void store_rec(R *dst, const R *src) {
+    constexpr int B = REC * int(sizeof(R));
+    if constexpr (B % 16 == 0 && sizeof(R) == 4) {
+#pragma unroll
+        for (int i = 0; i < REC / 4; ++i)
+            reinterpret_cast<float4 *>(dst)[i] = make_float4(src[4 * i], src[4 * i + 1], src[4 * i + 2], src[4 * i + 3]);
+    } else if constexpr (B % 16 == 0 && sizeof(R) == 8) {
+#pragma unroll
+        for (int i = 0; i < REC / 2; ++i) reinterpret_cast<double2 *>(dst)[i] = make_double2(src[2 * i], src[2 * i + 1]);
+    } else if constexpr (B % 8 == 0 && sizeof(R) == 4) {
+#pragma unroll
+        for (int i = 0; i < REC / 2; ++i) reinterpret_cast<float2 *>(dst)[i] = make_float2(src[2 * i], src[2 * i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < REC; ++i) dst[i] = src[i];
+    }
+}
+
 // ---------------------------------------------------------------- model constants
 
 // k-invariant quantities, computed on the host in FP64 and rounded once to
@@ -672,12 +723,14 @@ KF_D void lowrank_core(const R *C, const R *U, R G[M * N], R Wp[M * (M + 1) / 2]
 }
 
 // Lemma 1, ei (x) ej, for a fresh right operand ej whose J is U^T U.
+// Fresh right operand given by its parts: A_j, C_j (packed), U from the model
+// constants, b_j and eta_j from registers.
 template <int N, int M, typename R, int MODE>
-KF_D void lemma1_lr(const FElem<N, R> &ei, const FElem<N, R> &ej, const R *U, FElem<N, R> &o) {
+KF_D void lemma1_lr_parts(const FElem<N, R> &ei, const R *Aj, const R *bj, const R *Cj, const R *etaj, const R *U,
+                          FElem<N, R> &o) {
     using E = FElem<N, R>;
     constexpr int SM = M * (M + 1) / 2;
     const R *Ai = ei.v + E::oA, *bi = ei.v + E::ob, *Ci = ei.v + E::oC, *etai = ei.v + E::oe, *Ji = ei.v + E::oJ;
-    const R *Aj = ej.v + E::oA, *bj = ej.v + E::ob, *Cj = ej.v + E::oC, *etaj = ej.v + E::oe;
     R G[M * N], W[SM];
     double ld;
     lowrank_core<N, M, R, MODE>(Ci, U, G, W, ld);
@@ -830,17 +883,21 @@ KF_D void lemma1_lr(const FElem<N, R> &ei, const FElem<N, R> &ej, const R *U, FE
         }
 }
 
+template <int N, int M, typename R, int MODE>
+KF_D void lemma1_lr(const FElem<N, R> &ei, const FElem<N, R> &ej, const R *U, FElem<N, R> &o) {
+    using E = FElem<N, R>;
+    lemma1_lr_parts<N, M, R, MODE>(ei, ej.v + E::oA, ej.v + E::ob, ej.v + E::oC, ej.v + E::oe, U, o);
+}
+
 // (b, C) half of Lemma 1 for a fresh right operand: c <- c (x) ej.  With LL
 // it also returns, for ytil = L^{-1} y_k, the whitened innovation
 // vt = ytil - U b (before the update) and vt^T W vt and log det(I_m + U C U^T),
 // which give log N(y_k; H F b, S_k) since S_k = L (I_m + U C U^T) L^T.
 template <int N, int M, typename R, int MODE, bool LL>
-KF_D void apply_fwd_lr(FwdCarry<N, R> &c, const FElem<N, R> &ej, const R *U, const R *ytil, R *quad,
-                       double *logdet) {
-    using E = FElem<N, R>;
+KF_D void apply_fwd_lr_parts(FwdCarry<N, R> &c, const R *Aj, const R *bj, const R *Cj, const R *etaj, const R *U,
+                             const R *ytil, R *quad, double *logdet) {
     using CT = FwdCarry<N, R>;
     const R *b = c.v + CT::ob, *C = c.v + CT::oC;
-    const R *Aj = ej.v + E::oA, *bj = ej.v + E::ob, *Cj = ej.v + E::oC, *etaj = ej.v + E::oe;
     R G[M * N], W[M * (M + 1) / 2];
     double ld;
     lowrank_core<N, M, R, MODE>(C, U, G, W, ld);
@@ -926,6 +983,14 @@ KF_D void apply_fwd_lr(FwdCarry<N, R> &c, const FElem<N, R> &ej, const R *U, con
             for (int k = 0; k < N; ++k) s += AD[r * N + k] * Aj[q * N + k];
             c.v[CT::oC + su(N, r, q)] = s;
         }
+}
+
+template <int N, int M, typename R, int MODE, bool LL>
+KF_D void apply_fwd_lr(FwdCarry<N, R> &c, const FElem<N, R> &ej, const R *U, const R *ytil, R *quad,
+                       double *logdet) {
+    using E = FElem<N, R>;
+    apply_fwd_lr_parts<N, M, R, MODE, LL>(c, ej.v + E::oA, ej.v + E::ob, ej.v + E::oC, ej.v + E::oe, U, ytil, quad,
+                                          logdet);
 }
 
 // ---------------------------------------------------------------- Lemma 2
@@ -1021,7 +1086,10 @@ KF_D void build_filter_elem(const FiltParams<N, R> &P, int64_t k, const R *yk, F
     const int ny = P.ny;
     R y[MAXNY];
 #pragma unroll
-    for (int j = 0; j < MAXNY; ++j) y[j] = (j < ny) ? yk[j] : R(0);
+    for (int j = 0; j < MAXNY; ++j) y[j] = 0;
+#pragma unroll
+    for (int j = 0; j < MAXNY; ++j)
+        if (j < ny) y[j] = yk[j];
     const bool first = (k == 1);
 #pragma unroll
     for (int r = 0; r < N; ++r) {
@@ -1042,6 +1110,26 @@ KF_D void build_filter_elem(const FiltParams<N, R> &P, int64_t k, const R *yk, F
     for (int i = 0; i < E::S; ++i) {
         e.v[E::oC + i] = first ? P.C1[i] : P.C[i];
         e.v[E::oJ + i] = P.J[i];
+    }
+}
+
+// (b_k, eta_k) of a fresh element a_k, k >= 2 (Eq. pkf_init1, Eq. pkf_init3),
+// for a compile-time number of measurements M: b_k = K y_k, eta_k = G y_k.
+template <int N, int M, typename R>
+KF_D void fresh_b_eta(const FiltParams<N, R> &P, const R *yk, R *b, R *eta) {
+    R y[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) y[j] = yk[j];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R sb = 0, se = 0;
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            sb += P.K[r * MAXNY + j] * y[j];
+            se += P.G[r * MAXNY + j] * y[j];
+        }
+        b[r] = sb;
+        eta[r] = se;
     }
 }
 

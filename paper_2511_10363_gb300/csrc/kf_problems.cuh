@@ -199,20 +199,21 @@ struct FilterFwd {
     using Elem = FElem<N, R>;
     using Carry = FwdCarry<N, R>;
     static constexpr int S = N * (N + 1) / 2;
-    static constexpr int IN_REC = 0, O1 = FRec<N, R>::SIZE, O2 = N, O3 = N * N;
+    // the low-rank path knows ny = LR at compile time and stages y as its input record
+    static constexpr int IN_REC = LR, O1 = FRec<N, R>::SIZE, O2 = N, O3 = N * N;
     struct Args {
         Src src;
         KfBufs<R> buf;
         int want_ll;
     };
     static KF_HD int64_t total(const Args &a) { return seq_total(a.src); }
-    static KF_HD const R *in_arr(const Args &) { return nullptr; }
+    static KF_HD const R *in_arr(const Args &a) { return LR > 0 ? a.buf.y : nullptr; }
     static KF_HD R *out_arr(const Args &a, int i) { return i == 0 ? a.buf.frec : i == 1 ? a.buf.mf_user : a.buf.Pf_user; }
     static KF_D SegCursor cursor(const Args &a, int64_t p) { return seg_find(a.src, p); }
-    static KF_D void build(const Args &a, int64_t p, SegCursor &cur, const R *, Elem &e) {
+    static KF_D void build(const Args &a, int64_t p, SegCursor &cur, const R *in, Elem &e) {
         seg_move(a.src, cur, p);
         const FiltParams<N, R> &P = seg_params(a.src, cur);
-        build_filter_elem<N, R>(P, p - cur.b + 1, a.buf.y + p * P.ny, e);
+        build_filter_elem<N, R>(P, p - cur.b + 1, y_of(a, p, in, P.ny), e);
     }
     static KF_D void combine(const Elem &x, const Elem &y, Elem &o) { op_lemma1<N, R, MODE>(x, y, o); }
     // x (x) y where y is the element of position p (fresh)
@@ -236,22 +237,103 @@ struct FilterFwd {
     static KF_D void emit(const Args &, const Carry &c, const R *, R *o1, R *o2, R *o3) {
         const R *b = c.v + Carry::ob, *C = c.v + Carry::oC;
         if (o1) {
+            R rec[O1];
 #pragma unroll
-            for (int i = 0; i < N; ++i) o1[i] = b[i];
+            for (int i = 0; i < N; ++i) rec[i] = b[i];
 #pragma unroll
-            for (int i = 0; i < S; ++i) o1[N + i] = C[i];
+            for (int i = 0; i < S; ++i) rec[N + i] = C[i];
+#pragma unroll
+            for (int i = N + S; i < O1; ++i) rec[i] = 0;
+            store_rec<O1>(o1, rec);
         }
-        if (o2) {
-#pragma unroll
-            for (int i = 0; i < N; ++i) o2[i] = b[i];
+        if (o2) store_rec<N>(o2, b);
+        if (o3) {
+            R full[N * N];
+            store_full<N>(full, C);
+            store_rec<N * N>(o3, full);
         }
-        if (o3) store_full<N>(o3, C);
+    }
+    // measurement of position p: staged record (low-rank path) or device memory
+    static KF_D const R *y_of(const Args &a, int64_t p, const R *in, int ny) {
+        return (LR > 0 && in) ? in : a.buf.y + p * ny;
+    }
+    // agg <- agg (x) a_p
+    static KF_D void fold_at(const Args &a, int64_t p, SegCursor &cur, const R *in, Elem &agg) {
+        if constexpr (LR > 0) {
+            seg_move(a.src, cur, p);
+            const FiltParams<N, R> &P = seg_params(a.src, cur);
+            if (p != cur.b) {
+                R yv[LR], b[N], eta[N];
+                load_rec<LR>(yv, y_of(a, p, in, LR));
+                fresh_b_eta<N, LR, R>(P, yv, b, eta);
+                Elem t;
+                if constexpr (N >= 8) {
+                    Elem e;
+                    build_filter_elem<N, R>(P, 2, yv, e);
+                    op_lemma1_lr<N, LR, R, MODE>(agg, e, P.U, t);
+                } else {
+                    lemma1_lr_parts<N, LR, R, MODE>(agg, P.A, b, P.C, eta, P.U, t);
+                }
+                agg = t;
+                return;
+            }
+        }
+        Elem e, t;
+        build(a, p, cur, in, e);
+        fold(a, cur, agg, e, t);
+        agg = t;
     }
     // log p(y_k | y_{1:k-1}) from the prefix carry c = s_{k-1} before a_k is
     // applied.  k = 1: v = y_1 - H xbar_{1|0}, S_1 precomputed.  k >= 2:
     // S_k = S + HF C F^T H^T, so det S_k = det S det(I + C J) and, with
     // w = eta_k - J b = F^T H^T S^{-1} v, v^T S_k^{-1} v = v^T S^{-1} v - w^T D w,
     // D = (I + C J)^{-1} C (matrix determinant lemma and Woodbury identity).
+    // c <- c (x) a_p, outputs of p, log-likelihood term of p
+    static KF_D double step_at(const Args &a, int64_t p, SegCursor &cur, Carry &c, const R *in, R *o1, R *o2, R *o3) {
+        if constexpr (LR > 0) {
+            seg_move(a.src, cur, p);
+            const FiltParams<N, R> &P = seg_params(a.src, cur);
+            if (p != cur.b) {
+                R yv[LR], b[N], eta[N];
+                load_rec<LR>(yv, y_of(a, p, in, LR));
+                fresh_b_eta<N, LR, R>(P, yv, b, eta);
+                double ll = 0.0;
+                if (a.want_ll) {
+                    R yt[LR];
+#pragma unroll
+                    for (int i = 0; i < LR; ++i) {
+                        R s = 0;
+#pragma unroll
+                        for (int k = 0; k <= i; ++k) s += P.Linv[i * MAXNY + k] * yv[k];
+                        yt[i] = s;
+                    }
+                    R q;
+                    double ld;
+                    if constexpr (N >= 8) {
+                        Elem e;
+                        build_filter_elem<N, R>(P, 2, yv, e);
+                        op_apply_fwd_lr<N, LR, R, MODE, true>(c, e, P.U, yt, &q, &ld);
+                    } else {
+                        apply_fwd_lr_parts<N, LR, R, MODE, true>(c, P.A, b, P.C, eta, P.U, yt, &q, &ld);
+                    }
+                    ll = -0.5 * (double(q) + ld + P.llc);
+                } else {
+                    if constexpr (N >= 8) {
+                        Elem e;
+                        build_filter_elem<N, R>(P, 2, yv, e);
+                        op_apply_fwd_lr<N, LR, R, MODE, false>(c, e, P.U, nullptr, nullptr, nullptr);
+                    } else {
+                        apply_fwd_lr_parts<N, LR, R, MODE, false>(c, P.A, b, P.C, eta, P.U, nullptr, nullptr, nullptr);
+                    }
+                }
+                emit(a, c, in, o1, o2, o3);
+                return ll;
+            }
+        }
+        Elem e;
+        build(a, p, cur, in, e);
+        return step(a, p, cur, c, e, in, o1, o2, o3);
+    }
     static KF_D double step(const Args &a, int64_t p, SegCursor &cur, Carry &c, const Elem &e, const R *in, R *o1,
                             R *o2, R *o3) {
         if (!a.want_ll) {
@@ -261,7 +343,7 @@ struct FilterFwd {
         }
         const FiltParams<N, R> &P = seg_params(a.src, cur);
         const int ny = P.ny;
-        const R *yk = a.buf.y + p * ny;
+        const R *yk = y_of(a, p, in, ny);
         double ll;
         if (p == cur.b) {
             R v[MAXNY];
@@ -357,15 +439,23 @@ struct TfRev {
     }
     // merge with the filter record (Eqs. mean_tf_combination / cov_tf_combination)
     static KF_D void emit(const Args &, const Carry &c, const R *in, R *o1, R *o2, R *) {
-        R x[N], Pk[S], ms[N], Ps[S];
-#pragma unroll
-        for (int i = 0; i < N; ++i) x[i] = in[i];
-#pragma unroll
-        for (int i = 0; i < S; ++i) Pk[i] = in[N + i];
-        op_tf_merge<N, R, MODE>(x, Pk, c, ms, Ps);
-#pragma unroll
-        for (int i = 0; i < N; ++i) o1[i] = ms[i];
-        store_full<N>(o2, Ps);
+        R rec[IN_REC], ms[N], Ps[S], full[N * N];
+        load_rec<IN_REC>(rec, in);
+        op_tf_merge<N, R, MODE>(rec, rec + N, c, ms, Ps);
+        store_rec<N>(o1, ms);
+        store_full<N>(full, Ps);
+        store_rec<N * N>(o2, full);
+    }
+    static KF_D void fold_at(const Args &a, int64_t p, SegCursor &cur, const R *in, Elem &agg) {
+        Elem e, t;
+        build(a, p, cur, in, e);
+        combine(agg, e, t);
+        agg = t;
+    }
+    static KF_D double step_at(const Args &a, int64_t p, SegCursor &cur, Carry &c, const R *in, R *o1, R *o2, R *o3) {
+        Elem e;
+        build(a, p, cur, in, e);
+        return step(a, p, cur, c, e, in, o1, o2, o3);
     }
     static KF_D double step(const Args &a, int64_t, SegCursor &, Carry &c, const Elem &e, const R *in, R *o1, R *o2,
                             R *o3) {
@@ -399,12 +489,20 @@ struct RtsRev {
         const int64_t g = seq_total(a.src) - 1 - p;
         seg_move(a.src, cur, g);
         const FiltParams<N, R> &P = seg_params(a.src, cur);
-        R x[N], Pk[S];
-#pragma unroll
-        for (int i = 0; i < N; ++i) x[i] = in[i];
-#pragma unroll
-        for (int i = 0; i < S; ++i) Pk[i] = in[N + i];
-        op_build_rts<N, R>(P, g == cur.e - 1, x, Pk, e);
+        R rec[IN_REC];
+        load_rec<IN_REC>(rec, in);
+        op_build_rts<N, R>(P, g == cur.e - 1, rec, rec + N, e);
+    }
+    static KF_D void fold_at(const Args &a, int64_t p, SegCursor &cur, const R *in, Elem &agg) {
+        Elem e, t;
+        build(a, p, cur, in, e);
+        combine(agg, e, t);
+        agg = t;
+    }
+    static KF_D double step_at(const Args &a, int64_t p, SegCursor &cur, Carry &c, const R *in, R *o1, R *o2, R *o3) {
+        Elem e;
+        build(a, p, cur, in, e);
+        return step(a, p, cur, c, e, in, o1, o2, o3);
     }
     static KF_D void combine(const Elem &x, const Elem &y, Elem &o) { op_lemma2<N, R>(y, x, o); }
     static KF_D void fold(const Args &, const SegCursor &, const Elem &x, const Elem &y, Elem &o) { combine(x, y, o); }
@@ -416,9 +514,10 @@ struct RtsRev {
         for (int i = 0; i < S; ++i) c.v[Carry::oL + i] = e.v[Elem::oL + i];
     }
     static KF_D void emit(const Args &, const Carry &c, const R *, R *o1, R *o2, R *) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) o1[i] = c.v[Carry::og + i];
-        store_full<N>(o2, c.v + Carry::oL);
+        R full[N * N];
+        store_rec<N>(o1, c.v + Carry::og);
+        store_full<N>(full, c.v + Carry::oL);
+        store_rec<N * N>(o2, full);
     }
     static KF_D double step(const Args &a, int64_t, SegCursor &, Carry &c, const Elem &e, const R *in, R *o1, R *o2,
                             R *o3) {

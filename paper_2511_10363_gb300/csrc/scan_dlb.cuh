@@ -46,6 +46,9 @@ struct DlbCtl {
     // per-warp dynamic shared memory: byte offsets of the staging buffers
     // (input double buffer, three outputs; -1 = absent) and the warp stride
     int sm_in0, sm_in1, sm_out[3], sm_warp;
+    int lbw;               // warps that take part in the look-back (1 .. THREADS/32)
+    uint64_t *trace;       // optional [ntiles][8] %globaltimer stamps at phase boundaries
+    int trace_cap;         // tiles the trace buffer holds
 };
 
 constexpr int KF_STATUS_TIMEOUT = 5;
@@ -135,6 +138,8 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
     __syncthreads();
     const int tile = s_tile;
     if (tile >= ctl.ntiles || tile == ctl.inject_skip_tile) return;
+    uint64_t *const trace = (ctl.trace && tile < ctl.trace_cap && threadIdx.x == 0) ? ctl.trace + 8 * tile : nullptr;
+    if (trace) trace[0] = global_ns();
     const int64_t total = P::total(args);
     const int64_t start = (int64_t(tile) * THREADS + tid) * ctl.K;
     const int64_t end = start + ctl.K < total ? start + ctl.K : total;
@@ -176,10 +181,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
                     P::build(args, p, cur, in, agg);
                     have = true;
                 } else {
-                    Elem e, t;
-                    P::build(args, p, cur, in, e);
-                    P::fold(args, cur, agg, e, t);
-                    agg = t;
+                    P::fold_at(args, p, cur, in, agg);
                 }
             }
             __syncwarp();
@@ -204,6 +206,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
         for (int i = 0; i < ES; ++i) s_wx[warp][i] = agg.v[i];
     }
     __syncthreads();
+    if (trace) trace[1] = global_ns();
     if (warp == 0) {
         Elem w;
         if (lane < NW) {
@@ -247,75 +250,83 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
     }
     __syncthreads();
     if (tile > 0 && tid == 0) st_release(ctl.flags + tile, 1);
+    if (trace) trace[2] = global_ns();
 
     // ---- 4. look-back
     Carry tc;
     set_zero(tc);
     if (tile > 0) {
-        // predecessors q = tile-1-(tid*vv + v), v < vv; vv*THREADS >= ntiles
-        const int vv = (ctl.ntiles + THREADS - 1) / THREADS;
+        // the first lbw warps take the predecessors: thread tid < 32*lbw takes
+        // q = tile-1-(tid*vv + v), v < vv, with vv*32*lbw >= ntiles
+        const int lbt = 32 * ctl.lbw;
+        const int vv = (ctl.ntiles + lbt - 1) / lbt;
+        const bool lbthread = tid < lbt;
         int qloc = -1;
+        if (lbthread) {
 #pragma unroll 1
-        for (int v = 0; v < vv; ++v) {
-            const int q = tile - 1 - (tid * vv + v);
-            if (q >= 0) {
-                const int f = wait_flag(ctl.flags + q, ctl);
-                if (f == 0) s_abort = 1;
-                if (f == 2 && q > qloc) qloc = q;
+            for (int v = 0; v < vv; ++v) {
+                const int q = tile - 1 - (tid * vv + v);
+                if (q >= 0) {
+                    const int f = wait_flag(ctl.flags + q, ctl);
+                    if (f == 0) s_abort = 1;
+                    if (f == 2 && q > qloc) qloc = q;
+                }
             }
         }
         if (qloc >= 0) atomicMax(&s_qstar, qloc);
         __syncthreads();
         if (s_abort) return;
         const int qstar = s_qstar;
-        // fold the aggregates of my predecessors after qstar, earliest first
-        Elem x;
-        bool have = false;
+        if (lbthread) {
+            // fold the aggregates of my predecessors after qstar, earliest first
+            Elem x;
+            bool have = false;
 #pragma unroll 1
-        for (int v = vv - 1; v >= 0; --v) {
-            const int q = tile - 1 - (tid * vv + v);
-            if (q > qstar) {
-                Elem a;
-                load_cg(a, static_cast<const R *>(ctl.agg) + int64_t(q) * ES);
-                if (!have) {
-                    x = a;
-                    have = true;
-                } else {
-                    Elem t;
-                    P::combine(x, a, t);
+            for (int v = vv - 1; v >= 0; --v) {
+                const int q = tile - 1 - (tid * vv + v);
+                if (q > qstar) {
+                    Elem a;
+                    load_cg(a, static_cast<const R *>(ctl.agg) + int64_t(q) * ES);
+                    if (!have) {
+                        x = a;
+                        have = true;
+                    } else {
+                        Elem t;
+                        P::combine(x, a, t);
+                        x = t;
+                    }
+                }
+            }
+            if (!have) set_identity(x);
+            // lane l covers later tiles than lane l+1: suffix reduction to lane 0
+#pragma unroll 1
+            for (int s = 1; s < 32; s <<= 1) {
+                Elem o, t;
+                shfl_down_x(x, o, s);
+                if (lane + s < 32) {
+                    P::combine(o, x, t);
                     x = t;
                 }
             }
-        }
-        if (!have) set_identity(x);
-        // lane l covers later tiles than lane l+1: suffix reduction to lane 0
-#pragma unroll 1
-        for (int s = 1; s < 32; s <<= 1) {
-            Elem o, t;
-            shfl_down_x(x, o, s);
-            if (lane + s < 32) {
-                P::combine(o, x, t);
-                x = t;
-            }
-        }
-        if (lane == 0) {
+            if (lane == 0) {
 #pragma unroll
-            for (int i = 0; i < ES; ++i) s_red[warp][i] = x.v[i];
+                for (int i = 0; i < ES; ++i) s_red[warp][i] = x.v[i];
+            }
         }
         __syncthreads();
         if (warp == 0) {
             Elem y;
-            if (lane < NW) {
+            if (lane < ctl.lbw) {
 #pragma unroll
                 for (int i = 0; i < ES; ++i) y.v[i] = s_red[lane][i];
             } else {
                 set_identity(y);
             }
 #pragma unroll 1
-            for (int s = 1; s < NW; s <<= 1) {
+            for (int s = 1; s < ctl.lbw; s <<= 1) {
                 Elem o, t;
                 shfl_down_x(y, o, s);
-                if (lane + s < NW) {
+                if (lane + s < ctl.lbw) {
                     P::combine(o, y, t);
                     y = t;
                 }
@@ -339,6 +350,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
         }
     }
     __syncthreads();
+    if (trace) trace[3] = global_ns();
 
     // ---- 6. carries and the fused extraction pass
     Carry c;
@@ -385,9 +397,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
                 R *o1 = obuf[0] ? stage_rec<C, (P::O1 ? P::O1 : 1), R>(obuf[0], lane, slot) : nullptr;
                 R *o2 = obuf[1] ? stage_rec<C, (P::O2 ? P::O2 : 1), R>(obuf[1], lane, slot) : nullptr;
                 R *o3 = obuf[2] ? stage_rec<C, (P::O3 ? P::O3 : 1), R>(obuf[2], lane, slot) : nullptr;
-                Elem e;
-                P::build(args, p, cur, in, e);
-                ll += P::step(args, p, cur, c, e, in, o1, o2, o3);
+                ll += P::step_at(args, p, cur, c, in, o1, o2, o3);
             }
             __syncwarp();
             const int64_t gs = seg_first<P, C>(total, start + ch * C);
@@ -397,6 +407,8 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
             __syncwarp();
         }
     }
+
+    if (trace) trace[4] = global_ns();
 
     // ---- log-likelihood: fixed-order reduction per tile, then over tiles
     if (ctl.ll_out) {
