@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
         if (qloc >= 0) atomicMax(&s_qstar, qloc);
         __syncthreads();
         if (s_abort) return;
+        if (trace) trace[5] = global_ns();
         const int qstar = s_qstar;
         if (lbthread) {
             // fold the aggregates of my predecessors after qstar, earliest first
@@ -298,6 +299,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
                 }
             }
             if (!have) set_identity(x);
+            if (trace) trace[6] = global_ns();
             // lane l covers later tiles than lane l+1: suffix reduction to lane 0
 #pragma unroll 1
             for (int s = 1; s < 32; s <<= 1) {
@@ -314,6 +316,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
             }
         }
         __syncthreads();
+        if (trace) trace[7] = global_ns();
         if (warp == 0) {
             Elem y;
             if (lane < ctl.lbw) {
