@@ -82,7 +82,8 @@ typedef enum {
     KF_ERR_OOM = 4,      /* device allocation failed                         */
     KF_ERR_TIMEOUT = 5,  /* a bounded inter-block wait in a kernel ran out   */
     KF_ERR_BUDGET = 6,   /* serving: job larger than the device budget       */
-    KF_ERR_BUSY = 7      /* serving: queue full / unknown job id             */
+    KF_ERR_BUSY = 7,     /* serving: queue full / unknown job id             */
+    KF_ERR_CAPACITY = 8  /* request larger than a fixed scratch capacity     */
 } kf_status_t;
 
 typedef struct {
@@ -124,6 +125,43 @@ kf_status_t kf_two_filter_smooth(const kf_model_t *model, int64_t T, const void 
                                  kf_precision_t prec, kf_scan_t scan, void *ms_out, void *Ps_out,
                                  void *mf_out, void *Pf_out, double *loglik, void *workspace,
                                  void *stream);
+
+/* RTS smoother that allocates no device memory.
+ *
+ * The paper has no counterpart: this is a deployment variant of
+ * kf_rts_smooth for callers that may not allocate device memory at call
+ * time -- for example code whose device memory is all owned and accounted
+ * for by another allocator (a framework's memory pool or a fixed budget),
+ * or a latency-critical loop that cannot afford cudaMalloc's implicit
+ * device-wide synchronisation or the risk of an out-of-memory failure in
+ * the middle of its work.
+ *
+ * It computes exactly what kf_rts_smooth computes with the decoupled
+ * look-back scan, but its scratch (look-back descriptors, the filter records
+ * handed from the forward to the backward pass, and its status word) lives
+ * in one statically sized device array of KF_NOALLOC_SCRATCH_BYTES that the
+ * library declares at file scope; every GPU that loads the library holds
+ * that array until the process exits.  The call makes no cudaMalloc or
+ * cudaFree and no other allocating call, not even on its first use.
+ *   - The caller still passes y, ms_out [T][nx] and Ps_out [T][nx][nx]
+ *     (device, working precision), and may pass loglik (device double) and
+ *     status_out (device int, may be NULL): status_out is set to 0 at the
+ *     start of the call and receives KF_ERR_TIMEOUT if a bounded wait in a
+ *     kernel runs out.
+ *   - Its first call on a device looks up the device address of the array
+ *     (cudaGetSymbolAddress); make that first call before capturing the
+ *     stream into a graph.
+ *   - Requests whose scratch would exceed the array (kf_workspace_size of an
+ *     RTS call plus 256 bytes, i.e. about T <= 255,000 steps at nx = 4 in
+ *     FP32) return KF_ERR_CAPACITY and enqueue nothing; kf_timing_enable
+ *     must be off (KF_ERR_ARG otherwise).
+ *   - All calls share the one array, which keeps the last call's contents;
+ *     the call clears what must start at zero.  Calls whose work overlaps on
+ *     the GPU (different streams, or different host threads) race on the
+ *     array and must be serialised by the caller. */
+#define KF_NOALLOC_SCRATCH_BYTES (16u << 20)
+kf_status_t kf_rts_smooth_noalloc(const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec,
+                                  void *ms_out, void *Ps_out, double *loglik, int *status_out, void *stream);
 
 /* Waits for `stream`, then returns and clears the device status word of the
  * current device: KF_OK, or KF_ERR_TIMEOUT if some kernel's bounded wait ran

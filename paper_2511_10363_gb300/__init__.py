@@ -28,7 +28,7 @@ SCANS = {"auto": 0, "dlb": 1, "decoupled_lookback": 1, "hillis_steele": 2, "hs":
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_fp64solve": 2, "mixed": 2}
 OPS = {"filter": 0, "rts": 1, "two_filter": 2, "tf": 2}
 STATUS = {0: "KF_OK", 1: "KF_ERR_ARG", 2: "KF_ERR_NOT_PD", 3: "KF_ERR_CUDA", 4: "KF_ERR_OOM",
-          5: "KF_ERR_TIMEOUT", 6: "KF_ERR_BUDGET", 7: "KF_ERR_BUSY"}
+          5: "KF_ERR_TIMEOUT", 6: "KF_ERR_BUDGET", 7: "KF_ERR_BUSY", 8: "KF_ERR_CAPACITY"}
 OPTIONS = {"wait_timeout_ns": 0, "test_skip_tile": 1, "positions_per_thread": 2, "threads": 3, "general_solve": 4,
            "lookback_warps": 5}
 
@@ -77,6 +77,8 @@ def lib():
         L.kf_timing_read.argtypes = [i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
         L.kf_measure_fma_peak.argtypes = [i, ctypes.POINTER(ctypes.c_double)]
         L.kf_trace_phases.argtypes = [i, vp, i]
+        L.kf_rts_smooth_noalloc.argtypes = [MP, i64, vp, i, vp, vp, vp, vp, vp]
+        L.kf_rts_smooth_noalloc.restype = ctypes.c_int
         L.kf_trace_phases.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -262,3 +264,18 @@ def kf_trace_phases(kind, buf=None):
     of 8 * capacity entries) of a look-back scan kind."""
     cap = 0 if buf is None else buf.numel() // 8
     _check(lib().kf_trace_phases(int(kind), _ptr(buf), cap), "kf_trace_phases")
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def kf_rts_smooth_noalloc(model, y, precision, ms_out, Ps_out, loglik=None, status_out=None, stream=None):
+    """RTS smoother that allocates no device memory (kfscan.h): its scratch
+    is a fixed device array inside the library, so every output buffer must
+    be passed in.  loglik: CUDA float64 tensor [1] or None; status_out: CUDA
+    int32 tensor [1] or None (receives a kernel's bounded-wait status)."""
+    m, _ = _prep(model, y, precision)
+    rc = lib().kf_rts_smooth_noalloc(ctypes.byref(m.c), y.shape[0], _ptr(y), PRECISIONS[precision], _ptr(ms_out),
+                                     _ptr(Ps_out), _ptr(loglik), _ptr(status_out), _stream(stream))
+    _check(rc, "kf_rts_smooth_noalloc")
+    return ms_out, Ps_out

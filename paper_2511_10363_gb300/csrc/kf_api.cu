@@ -463,6 +463,74 @@ static kf_status_t fma_peak(double *out) {
     return KF_OK;
 }
 
+
+// ---------------------------------------------------------------- no-allocation entry point
+//
+// Scratch of kf_rts_smooth_noalloc: [0, 256) its status word, then the
+// workspace of one RTS call.  Declared at file scope, so every GPU that
+// loads the library holds it until exit.  In host code the name is only a
+// stand-in; the kernels get its device address, looked up once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[KF_NOALLOC_SCRATCH_BYTES];
+static unsigned char *g_noalloc_base[64];
+static std::mutex g_noalloc_mu;
+
+static kf_status_t noalloc_base(unsigned char **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return KF_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return KF_ERR_CUDA;
+        g_noalloc_base[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_base[dev];
+    return KF_OK;
+}
+
+static kf_status_t rts_noalloc(const kf_model_t *md, int64_t T, const void *y, kf_precision_t prec, void *ms,
+                               void *Ps, double *loglik, int *status_out, void *stream) {
+    kf_status_t s = check_model(md);
+    if (s != KF_OK) return s;
+    if (T < 1 || !y || !ms || !Ps) return KF_ERR_ARG;
+    if (prec != KF_FP64 && prec != KF_FP32 && prec != KF_FP32_FP64SOLVE) return KF_ERR_ARG;
+    const size_t w = (prec == KF_FP64) ? 8 : 4;
+    if (!aligned(y, w) || !aligned(ms, w) || !aligned(Ps, w)) return KF_ERR_ARG;
+    if ((loglik && !aligned(loglik, 8)) || (status_out && !aligned(status_out, 4))) return KF_ERR_ARG;
+    if (timing_on()) return KF_ERR_ARG;   // kernel timing would create CUDA events
+    const size_t need = 256 + ws_bytes_dispatch(md->nx, KF_OP_RTS_I, int(prec), KF_SCAN_DLB_I, T);
+    if (need > KF_NOALLOC_SCRATCH_BYTES) return KF_ERR_CAPACITY;
+    HostModel hm;
+    s = precompute(md, &hm);
+    if (s != KF_OK) return s;
+    unsigned char *base = nullptr;
+    s = noalloc_base(&base);
+    if (s != KF_OK) return s;
+    LaunchReq q;
+    memset(&q, 0, sizeof(q));
+    q.op = KF_OP_RTS_I;
+    q.prec = int(prec);
+    q.scan = KF_SCAN_DLB_I;
+    q.T = T;
+    q.hm = &hm;
+    q.y = y;
+    q.ms = ms;
+    q.Ps = Ps;
+    q.loglik = loglik;
+    q.ws = base + 256;
+    q.stream = static_cast<cudaStream_t>(stream);
+    q.status = status_out ? status_out : reinterpret_cast<int *>(base);
+    q.timeout_ns = g_opt[KF_OPT_WAIT_TIMEOUT_NS].load();
+    q.inject_skip_tile = int(g_opt[KF_OPT_TEST_SKIP_TILE].load());
+    q.k_override = int(g_opt[KF_OPT_POSITIONS_PER_THREAD].load());
+    q.threads = int(g_opt[KF_OPT_THREADS].load());
+    q.no_lowrank = int(g_opt[KF_OPT_GENERAL_SOLVE].load());
+    q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
+    // the status word must start at zero (the scans' descriptors are cleared per launch)
+    cudaError_t e = cudaMemsetAsync(q.status, 0, sizeof(int), q.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return from_cuda(launch_dispatch(q));
+}
 }  // namespace kfs
 
 using namespace kfs;
@@ -479,6 +547,7 @@ const char *kf_status_string(kf_status_t s) {
         case KF_ERR_TIMEOUT: return "bounded wait timed out in a kernel";
         case KF_ERR_BUDGET: return "job exceeds the device memory budget";
         case KF_ERR_BUSY: return "queue full or unknown job";
+        case KF_ERR_CAPACITY: return "request exceeds a fixed scratch capacity";
     }
     return "unknown status";
 }
@@ -509,6 +578,11 @@ kf_status_t kf_two_filter_smooth(const kf_model_t *model, int64_t T, const void 
                                  kf_scan_t scan, void *ms_out, void *Ps_out, void *mf_out, void *Pf_out,
                                  double *loglik, void *workspace, void *stream) {
     return run(KF_OP_TF_I, model, T, y, prec, scan, ms_out, Ps_out, mf_out, Pf_out, loglik, workspace, stream);
+}
+
+kf_status_t kf_rts_smooth_noalloc(const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec,
+                                  void *ms_out, void *Ps_out, double *loglik, int *status_out, void *stream) {
+    return rts_noalloc(model, T, y, prec, ms_out, Ps_out, loglik, status_out, stream);
 }
 
 kf_status_t kf_sync_status(void *stream) {

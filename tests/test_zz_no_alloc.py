@@ -1,0 +1,60 @@
+"""The no-allocation RTS smoother (kf_rts_smooth_noalloc) against the
+ordinary entry point.
+
+Some callers cannot allocate device memory during a call (their memory is
+owned by another allocator, or they cannot afford cudaMalloc's implicit
+synchronisation); kf_rts_smooth_noalloc serves them from a fixed scratch
+array inside the library.  This file is named so that pytest collects it
+last.  Each test makes two calls in a row through the C ABI and compares
+both with kf_rts_smooth on the same inputs, with the tolerances of the
+other parity tests, and must pass alone in a fresh process as well as after
+every other test."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_util import TOL, mean_err, cov_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision,nx,T", [("fp64", 4, 5000), ("fp32", 4, 100000), ("fp32", 8, 3000),
+                                            ("fp32_fp64solve", 2, 777)])
+def test_noalloc_matches_rts_smooth_twice(precision, nx, T):
+    import torch
+    import paper_2511_10363_gb300 as kf
+    from paper_2511_10363_gb300 import build
+    build.build()
+    model = W.cv_model() if nx == 4 else (W.random_stable_model(8, 4, seed=3) if nx == 8 else W.cv1d_model())
+    dt = kf.dtype_of(precision)
+    y = torch.tensor(W.simulate(model, T, seed=T), dtype=dt, device="cuda")
+    ref_m, ref_P, ref_ll = kf.kf_rts_smooth(model, y, precision, "dlb", loglik=True)
+    assert kf.kf_sync_status() == 0
+    ref_m, ref_P, ref_ll = ref_m.double().cpu().numpy(), ref_P.double().cpu().numpy(), float(ref_ll.item())
+    for _ in range(2):
+        ms = torch.full((T, nx), float("nan"), dtype=dt, device="cuda")
+        Ps = torch.full((T, nx, nx), float("nan"), dtype=dt, device="cuda")
+        ll = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        st = torch.full((1,), 77, dtype=torch.int32, device="cuda")
+        kf.kf_rts_smooth_noalloc(model, y, precision, ms, Ps, loglik=ll, status_out=st)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        m, P = ms.double().cpu().numpy(), Ps.double().cpu().numpy()
+        assert mean_err(m, ref_m, ref_P) <= TOL[precision]
+        assert cov_err(P, ref_P) <= TOL[precision]
+        tol_ll = 1e-9 if precision == "fp64" else 1e-3
+        assert abs(float(ll.item()) - ref_ll) <= tol_ll * max(1.0, abs(ref_ll))
+
+
+def test_noalloc_rejects_requests_beyond_its_scratch():
+    import torch
+    import paper_2511_10363_gb300 as kf
+    model = W.cv_model()
+    T = 1 << 20                      # needs ~64 MB of filter records: beyond the 16 MB array
+    y = torch.zeros((T, 2), dtype=torch.float32, device="cuda")
+    ms = torch.empty((T, 4), device="cuda")
+    Ps = torch.empty((T, 4, 4), device="cuda")
+    with pytest.raises(kf.KfError) as e:
+        kf.kf_rts_smooth_noalloc(model, y, "fp32", ms, Ps)
+    assert e.value.status == 8       # KF_ERR_CAPACITY
+    assert kf.kf_workspace_size("rts", 4, 2, T, "fp32", "dlb") + 256 > kf.NOALLOC_SCRATCH_BYTES
