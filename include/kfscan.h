@@ -126,6 +126,29 @@ kf_status_t kf_two_filter_smooth(const kf_model_t *model, int64_t T, const void 
                                  void *mf_out, void *Pf_out, double *loglik, void *workspace,
                                  void *stream);
 
+/* Batch of independent sequences (the segmented scan): sequence s is
+ * y[offsets[s] .. offsets[s+1]) of the concatenated device buffer y
+ * [total][ny], total = offsets[nseq], and uses model
+ * models[model_of_seq[s]] (model_of_seq NULL: every sequence uses
+ * models[0]).  All models share nx and ny; each carries its own F, Q, H, R
+ * and prior m0, P0.  op selects Alg. pkf (m_out/P_out = filtering means and
+ * covariances, P_out may be NULL), Alg. prts or Alg. ptf (smoothed means
+ * and covariances).  Outputs are concatenated like y.  loglik, when not
+ * NULL, is a DEVICE array [nseq] receiving log p(y_{1:T_s}) per sequence,
+ * each summed in FP64 in a fixed order.  offsets and model_of_seq are HOST
+ * arrays copied during the call; offsets[0] = 0, non-decreasing (empty
+ * sequences allowed, total >= 1).  The scan is the decoupled look-back scan
+ * over the concatenation, one kernel per pass: no segment flags are needed
+ * because the operators reset at a sequence start (A_1 = 0), at a
+ * sequence end (E_T = 0) and at the two-filter terminal element
+ * e = (0, 0, 0, 0, 0).  Workspace as for the single-sequence calls, sized by
+ * kf_batch_workspace_size. */
+size_t kf_batch_workspace_size(kf_op_t op, int nx, int ny, int64_t total_steps, int nseq, int nmodels,
+                               kf_precision_t prec, int with_loglik);
+kf_status_t kf_batch_smooth(kf_op_t op, const kf_model_t *models, int nmodels, const int32_t *model_of_seq,
+                            int nseq, const int64_t *offsets, const void *y, kf_precision_t prec, void *m_out,
+                            void *P_out, double *loglik, void *workspace, void *stream);
+
 /* RTS smoother that allocates no device memory.
  *
  * The paper has no counterpart: this is a deployment variant of

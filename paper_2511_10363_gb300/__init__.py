@@ -78,6 +78,10 @@ def lib():
         L.kf_measure_fma_peak.argtypes = [i, ctypes.POINTER(ctypes.c_double)]
         L.kf_trace_phases.argtypes = [i, vp, i]
         L.kf_rts_smooth_noalloc.argtypes = [MP, i64, vp, i, vp, vp, vp, vp, vp]
+        L.kf_batch_smooth.argtypes = [i, MP, i, vp, i, vp, vp, i, vp, vp, vp, vp, vp]
+        L.kf_batch_smooth.restype = ctypes.c_int
+        L.kf_batch_workspace_size.argtypes = [i, i, i, i64, i, i, i, i]
+        L.kf_batch_workspace_size.restype = ctypes.c_size_t
         L.kf_rts_smooth_noalloc.restype = ctypes.c_int
         L.kf_trace_phases.restype = ctypes.c_int
         _lib = L
@@ -279,3 +283,40 @@ def kf_rts_smooth_noalloc(model, y, precision, ms_out, Ps_out, loglik=None, stat
                                      _ptr(Ps_out), _ptr(loglik), _ptr(status_out), _stream(stream))
     _check(rc, "kf_rts_smooth_noalloc")
     return ms_out, Ps_out
+
+
+def kf_batch_workspace_size(op, nx, ny, total_steps, nseq, nmodels, precision="fp32", loglik=True):
+    return int(lib().kf_batch_workspace_size(OPS[op], nx, ny, int(total_steps), int(nseq), int(nmodels),
+                                             PRECISIONS[precision], 1 if loglik else 0))
+
+
+def kf_batch_smooth(op, models, offsets, y, precision="fp32", model_of=None, m_out=None, P_out=None, loglik=False,
+                    workspace=None, stream=None):
+    """Batch of sequences concatenated in y [total, ny] (segmented scan).
+    models: one model dict (or Model) or a list; offsets: int64 array
+    [nseq + 1]; model_of: int32 array [nseq] or None.  Returns (m, P, ll)."""
+    import torch
+    if isinstance(models, (list, tuple)):
+        ms = [_as_model(m) for m in models]
+    else:
+        ms = [_as_model(models)]
+    arr = (_Model * len(ms))(*[m.c for m in ms])
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nseq = len(offs) - 1
+    mof = None if model_of is None else np.ascontiguousarray(np.asarray(model_of, dtype=np.int32))
+    dt = dtype_of(precision)
+    total = int(offs[-1])
+    if not (isinstance(y, torch.Tensor) and y.is_cuda and y.dtype == dt and y.is_contiguous()
+            and y.shape == (total, ms[0].ny)):
+        raise ValueError("y must be a contiguous CUDA tensor [total, ny] of dtype %s" % dt)
+    nx = ms[0].nx
+    if m_out is None:
+        m_out = torch.empty((total, nx), dtype=dt, device=y.device)
+    if P_out is None:
+        P_out = torch.empty((total, nx, nx), dtype=dt, device=y.device)
+    ll = torch.empty(nseq, dtype=torch.float64, device=y.device) if loglik else None
+    rc = lib().kf_batch_smooth(OPS[op], arr, len(ms), None if mof is None else mof.ctypes.data_as(ctypes.c_void_p),
+                               nseq, offs.ctypes.data_as(ctypes.c_void_p), _ptr(y), PRECISIONS[precision],
+                               _ptr(m_out), _ptr(P_out), _ptr(ll), _ptr(workspace), _stream(stream))
+    _check(rc, "kf_batch_smooth")
+    return m_out, P_out, ll

@@ -39,6 +39,24 @@ cudaError_t launch_dispatch(const LaunchReq &q) {
     return cudaErrorInvalidValue;
 }
 
+size_t batch_ws_bytes_dispatch(int nx, int op, int prec, int64_t T, int nseq, int nmodels, int loglik) {
+    switch (nx) {
+        case 2: KF_PREC_SWITCH(2, prec, batch_ws_bytes, op, T, nseq, nmodels, loglik)
+        case 4: KF_PREC_SWITCH(4, prec, batch_ws_bytes, op, T, nseq, nmodels, loglik)
+        case 8: KF_PREC_SWITCH(8, prec, batch_ws_bytes, op, T, nseq, nmodels, loglik)
+    }
+    return 0;
+}
+
+cudaError_t launch_batch_dispatch(const LaunchReq &q, const BatchReq &b) {
+    switch (q.hm->n) {
+        case 2: KF_PREC_SWITCH(2, q.prec, launch_batch, q, b)
+        case 4: KF_PREC_SWITCH(4, q.prec, launch_batch, q, b)
+        case 8: KF_PREC_SWITCH(8, q.prec, launch_batch, q, b)
+    }
+    return cudaErrorInvalidValue;
+}
+
 // ---------------------------------------------------------------- small FP64 host algebra
 
 static void mm(int r, int k, int c, const double *A, const double *B, double *C) {
@@ -464,6 +482,84 @@ static kf_status_t fma_peak(double *out) {
 }
 
 
+// ---------------------------------------------------------------- batches
+
+static kf_status_t run_batch(kf_op_t op, const kf_model_t *models, int nmodels, const int32_t *model_of, int nseq,
+                             const int64_t *offsets, const void *y, kf_precision_t prec, void *m1, void *P1,
+                             double *loglik, void *workspace, void *stream) {
+    if (op < KF_OP_FILTER || op > KF_OP_TWO_FILTER) return KF_ERR_ARG;
+    if (!models || nmodels < 1 || nseq < 1 || !offsets || !y || !m1) return KF_ERR_ARG;
+    if (op != KF_OP_FILTER && !P1) return KF_ERR_ARG;
+    if (prec != KF_FP64 && prec != KF_FP32 && prec != KF_FP32_FP64SOLVE) return KF_ERR_ARG;
+    if (offsets[0] != 0) return KF_ERR_ARG;
+    for (int s = 0; s < nseq; ++s)
+        if (offsets[s + 1] < offsets[s]) return KF_ERR_ARG;
+    const int64_t total = offsets[nseq];
+    if (total < 1 || total > (int64_t(1) << 40)) return KF_ERR_ARG;
+    const int nx = models[0].nx, ny = models[0].ny;
+    for (int i = 0; i < nmodels; ++i) {
+        if (models[i].nx != nx || models[i].ny != ny) return KF_ERR_ARG;
+        const kf_status_t s = check_model(&models[i]);
+        if (s != KF_OK) return s;
+    }
+    int *mof = static_cast<int *>(malloc(sizeof(int) * size_t(nseq)));
+    HostModel *hms = static_cast<HostModel *>(malloc(sizeof(HostModel) * size_t(nmodels)));
+    kf_status_t s = (mof && hms) ? KF_OK : KF_ERR_OOM;
+    for (int i = 0; s == KF_OK && i < nseq; ++i) {
+        mof[i] = model_of ? model_of[i] : 0;
+        if (mof[i] < 0 || mof[i] >= nmodels) s = KF_ERR_ARG;
+    }
+    for (int i = 0; s == KF_OK && i < nmodels; ++i) s = precompute(&models[i], &hms[i]);
+    const size_t w = (prec == KF_FP64) ? 8 : 4;
+    if (s == KF_OK && (!aligned(y, w) || !aligned(m1, w) || (P1 && !aligned(P1, w)) ||
+                       (loglik && !aligned(loglik, 8)) || (workspace && !aligned(workspace, 256))))
+        s = KF_ERR_ARG;
+    LaunchReq q;
+    memset(&q, 0, sizeof(q));
+    if (s == KF_OK) {
+        q.op = int(op);
+        q.prec = int(prec);
+        q.scan = KF_SCAN_DLB_I;
+        q.T = total;
+        q.hm = &hms[0];
+        q.y = y;
+        if (op == KF_OP_FILTER) {
+            q.mf_user = m1;
+            q.Pf_user = P1;
+        } else {
+            q.ms = m1;
+            q.Ps = P1;
+        }
+        q.loglik = loglik;
+        q.stream = static_cast<cudaStream_t>(stream);
+        q.timeout_ns = g_opt[KF_OPT_WAIT_TIMEOUT_NS].load();
+        q.inject_skip_tile = int(g_opt[KF_OPT_TEST_SKIP_TILE].load());
+        q.k_override = int(g_opt[KF_OPT_POSITIONS_PER_THREAD].load());
+        q.threads = int(g_opt[KF_OPT_THREADS].load());
+        q.no_lowrank = int(g_opt[KF_OPT_GENERAL_SOLVE].load());
+        q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
+        s = device_status_word(&q.status);
+    }
+    if (s == KF_OK) {
+        const size_t need = batch_ws_bytes_dispatch(nx, int(op), int(prec), total, nseq, nmodels, loglik != nullptr);
+        if (workspace) q.ws = workspace;
+        else s = library_workspace(need, &q.ws);
+    }
+    if (s == KF_OK) {
+        BatchReq b;
+        b.nseq = nseq;
+        b.nmodels = nmodels;
+        b.offsets = offsets;
+        b.model_of = mof;
+        b.hms = hms;
+        b.all_ny_half = (ny == nx / 2);
+        s = from_cuda(launch_batch_dispatch(q, b));
+    }
+    free(mof);
+    free(hms);
+    return s;
+}
+
 // ---------------------------------------------------------------- no-allocation entry point
 //
 // Scratch of kf_rts_smooth_noalloc: [0, 256) its status word, then the
@@ -578,6 +674,22 @@ kf_status_t kf_two_filter_smooth(const kf_model_t *model, int64_t T, const void 
                                  kf_scan_t scan, void *ms_out, void *Ps_out, void *mf_out, void *Pf_out,
                                  double *loglik, void *workspace, void *stream) {
     return run(KF_OP_TF_I, model, T, y, prec, scan, ms_out, Ps_out, mf_out, Pf_out, loglik, workspace, stream);
+}
+
+size_t kf_batch_workspace_size(kf_op_t op, int nx, int ny, int64_t total_steps, int nseq, int nmodels,
+                               kf_precision_t prec, int with_loglik) {
+    if ((nx != 2 && nx != 4 && nx != 8) || ny < 1 || ny > KF_MAXM || total_steps < 1 || nseq < 1 || nmodels < 1)
+        return 0;
+    if (op < KF_OP_FILTER || op > KF_OP_TWO_FILTER) return 0;
+    if (prec != KF_FP64 && prec != KF_FP32 && prec != KF_FP32_FP64SOLVE) return 0;
+    return batch_ws_bytes_dispatch(nx, int(op), int(prec), total_steps, nseq, nmodels, with_loglik ? 1 : 0);
+}
+
+kf_status_t kf_batch_smooth(kf_op_t op, const kf_model_t *models, int nmodels, const int32_t *model_of_seq, int nseq,
+                            const int64_t *offsets, const void *y, kf_precision_t prec, void *m_out, void *P_out,
+                            double *loglik, void *workspace, void *stream) {
+    return run_batch(op, models, nmodels, model_of_seq, nseq, offsets, y, prec, m_out, P_out, loglik, workspace,
+                     stream);
 }
 
 kf_status_t kf_rts_smooth_noalloc(const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec,

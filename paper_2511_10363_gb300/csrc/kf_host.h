@@ -54,6 +54,17 @@ struct LaunchReq {
     int threads;         // CTA size of the decoupled look-back scan (0: default)
     int no_lowrank;      // 1: use the general Lemma 1 solve even when ny = nx / 2
     int lookback_warps;  // warps of a CTA that take part in the look-back (0: all)
+    double *ll_step;     // per-step log-likelihood terms (batched calls; set by the batch launcher)
+};
+
+// A batch of sequences concatenated in y: sequence s covers
+// [offsets[s], offsets[s+1]) and uses model hms[model_of[s]].
+struct BatchReq {
+    int nseq, nmodels;
+    const int64_t *offsets;     // host [nseq + 1]
+    const int *model_of;        // host [nseq]
+    const HostModel *hms;       // host [nmodels]
+    int all_ny_half;            // every model has ny = nx / 2
 };
 
 bool debug_on();   // KFSCAN_DEBUG set in the environment
@@ -66,11 +77,15 @@ void timing_commit(int kind, cudaStream_t s, cudaEvent_t start);        // stop 
 void trace_target(int kind, uint64_t **buf, int *cap);                  // phase trace buffer of a scan kind
 size_t ws_bytes_dispatch(int nx, int op, int prec, int scan, int64_t T);
 cudaError_t launch_dispatch(const LaunchReq &q);
+size_t batch_ws_bytes_dispatch(int nx, int op, int prec, int64_t T, int nseq, int nmodels, int loglik);
+cudaError_t launch_batch_dispatch(const LaunchReq &q, const BatchReq &b);
 
 // per-(N, precision) entry points, one translation unit each (kf_n<N>_<p>.cu)
 #define KF_DECL_UNIT(N, P) \
     size_t ws_bytes_n##N##_##P(int op, int scan, int64_t T); \
-    cudaError_t launch_n##N##_##P(const LaunchReq &q);
+    cudaError_t launch_n##N##_##P(const LaunchReq &q); \
+    size_t batch_ws_bytes_n##N##_##P(int op, int64_t T, int nseq, int nmodels, int loglik); \
+    cudaError_t launch_batch_n##N##_##P(const LaunchReq &q, const BatchReq &b);
 KF_DECL_UNIT(2, f64) KF_DECL_UNIT(2, f32) KF_DECL_UNIT(2, mix)
 KF_DECL_UNIT(4, f64) KF_DECL_UNIT(4, f32) KF_DECL_UNIT(4, mix)
 KF_DECL_UNIT(8, f64) KF_DECL_UNIT(8, f32) KF_DECL_UNIT(8, mix)

@@ -198,6 +198,7 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
     ctl.incl = ws + L.incl;
     ctl.ll_part = reinterpret_cast<double *>(ws + L.llpart);
     ctl.ll_out = ll_out;
+    ctl.ll_step = q.ll_step;
     ctl.status = q.status;
     ctl.timeout_ns = q.timeout_ns;
     ctl.ntiles = tp.ntiles;
@@ -351,5 +352,105 @@ size_t ws_bytes_n(int op, int prec, int scan, int64_t T) {
     return ws_layout<N, float>(op, scan, T).total;
 }
 
+
+}  // namespace kfs
+
+namespace kfs {
+
+// ---------------------------------------------------------------- batches of sequences
+
+struct BatchLayout {
+    size_t base, offsets, model_of, params, ll_step, total;
+};
+
+template <int N, typename R>
+BatchLayout batch_layout(int op, int64_t total, int nseq, int nmodels, bool loglik) {
+    const WsLayout L = ws_layout<N, R>(op, KF_SCAN_DLB_I, total);
+    BatchLayout B;
+    size_t o = L.total;
+    B.base = 0;
+    B.offsets = o; o += al256(sizeof(int64_t) * (size_t(nseq) + 1));
+    B.model_of = o; o += al256(sizeof(int) * size_t(nseq));
+    B.params = o; o += al256(sizeof(FiltParams<N, R>) * size_t(nmodels));
+    B.ll_step = 0;
+    if (loglik) { B.ll_step = o; o += al256(sizeof(double) * size_t(total)); }
+    B.total = o;
+    return B;
+}
+
+template <int N, typename R, int MODE, int THREADS>
+static cudaError_t launch_batch_typed(const LaunchReq &q, const BatchReq &b) {
+    using Src = ManySeq<N, R>;
+    constexpr int V = (1024 + THREADS - 1) / THREADS;
+    const WsLayout L = ws_layout<N, R>(q.op, KF_SCAN_DLB_I, q.T);
+    const BatchLayout B = batch_layout<N, R>(q.op, q.T, b.nseq, b.nmodels, q.loglik != nullptr);
+    char *ws = static_cast<char *>(q.ws);
+    // stage the per-model constants, offsets and model indices into the workspace
+    FiltParams<N, R> *hp = static_cast<FiltParams<N, R> *>(malloc(sizeof(FiltParams<N, R>) * size_t(b.nmodels)));
+    if (!hp) return cudaErrorMemoryAllocation;
+    for (int i = 0; i < b.nmodels; ++i) to_params<N, R>(b.hms[i], hp[i]);
+    cudaError_t e = cudaMemcpyAsync(ws + B.params, hp, sizeof(FiltParams<N, R>) * size_t(b.nmodels),
+                                    cudaMemcpyHostToDevice, q.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + B.offsets, b.offsets, sizeof(int64_t) * (size_t(b.nseq) + 1), cudaMemcpyHostToDevice,
+                            q.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + B.model_of, b.model_of, sizeof(int) * size_t(b.nseq), cudaMemcpyHostToDevice,
+                            q.stream);
+    // the sources are pageable: each copy has been staged when it returns,
+    // so the host buffers may be released right away
+    free(hp);
+    if (e != cudaSuccess) return e;
+    Src src;
+    src.prm = reinterpret_cast<const FiltParams<N, R> *>(ws + B.params);
+    src.model_of = reinterpret_cast<const int *>(ws + B.model_of);
+    src.offsets = reinterpret_cast<const int64_t *>(ws + B.offsets);
+    src.nseg = b.nseq;
+    src.total = q.T;
+    KfBufs<R> buf;
+    buf.y = static_cast<const R *>(q.y);
+    buf.ms = static_cast<R *>(q.ms);
+    buf.Ps = static_cast<R *>(q.Ps);
+    buf.frec = (q.op == KF_OP_FILTER_I) ? nullptr : reinterpret_cast<R *>(ws + L.frec);
+    buf.mf_user = static_cast<R *>(q.mf_user);
+    buf.Pf_user = static_cast<R *>(q.Pf_user);
+    LaunchReq qq = q;
+    qq.scan = KF_SCAN_DLB_I;
+    qq.ll_step = q.loglik ? reinterpret_cast<double *>(ws + B.ll_step) : nullptr;
+    typename FilterFwd<N, R, MODE, Src>::Args fa;
+    fa.src = src;
+    fa.buf = buf;
+    fa.want_ll = q.loglik != nullptr;
+    constexpr int LRM = N / 2;
+    if (b.all_ny_half && !q.no_lowrank) {
+        typename FilterFwd<N, R, MODE, Src, LRM>::Args fl;
+        memcpy(&fl, &fa, sizeof(fl));
+        e = run_dlb<FilterFwd<N, R, MODE, Src, LRM>, THREADS, V>(fl, ws, L.ctl_f, L, qq, nullptr);
+    } else {
+        e = run_dlb<FilterFwd<N, R, MODE, Src>, THREADS, V>(fa, ws, L.ctl_f, L, qq, nullptr);
+    }
+    if (e != cudaSuccess) return e;
+    if (q.loglik) {
+        const int threads = 256, blocks = int((int64_t(b.nseq) * 32 + threads - 1) / threads);
+        segmented_ll_kernel<<<blocks, threads, 0, q.stream>>>(qq.ll_step, src.offsets, b.nseq, q.loglik);
+        count_launches(0, 1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (q.op == KF_OP_FILTER_I) return cudaSuccess;
+    qq.ll_step = nullptr;
+    if (q.op == KF_OP_RTS_I) {
+        typename RtsRev<N, R, Src>::Args ra;
+        ra.src = src;
+        ra.buf = buf;
+        ra.want_ll = 0;
+        return run_dlb<RtsRev<N, R, Src>, THREADS, V>(ra, ws, L.ctl_r, L, qq, nullptr);
+    }
+    typename TfRev<N, R, MODE, Src>::Args ta;
+    ta.src = src;
+    ta.buf = buf;
+    ta.want_ll = 0;
+    return run_dlb<TfRev<N, R, MODE, Src>, THREADS, V>(ta, ws, L.ctl_r, L, qq, nullptr);
+}
 
 }  // namespace kfs

@@ -10,4 +10,10 @@ cudaError_t launch_n4_f32(const LaunchReq &q) {
     return launch_typed<4, float, 0, 128>(q);
 }
 
+size_t batch_ws_bytes_n4_f32(int op, int64_t T, int nseq, int nmodels, int loglik) {
+    return batch_layout<4, float>(op, T, nseq, nmodels, loglik != 0).total;
+}
+
+cudaError_t launch_batch_n4_f32(const LaunchReq &q, const BatchReq &b) { return launch_batch_typed<4, float, 0, 128>(q, b); }
+
 }  // namespace kfs

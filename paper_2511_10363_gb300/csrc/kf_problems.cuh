@@ -35,8 +35,9 @@ struct OneSeq {
 
 template <int N, typename R>
 struct ManySeq {
-    const FiltParams<N, R> *prm;   // [nseg]
-    const int64_t *offsets;        // [nseg + 1], offsets[0] = 0
+    const FiltParams<N, R> *prm;   // [nmodels]
+    const int *model_of;           // [nseg] model of each sequence
+    const int64_t *offsets;        // [nseg + 1], offsets[0] = 0, non-decreasing
     int nseg;
     int64_t total;
 };
@@ -51,7 +52,7 @@ struct SegCursor {
 template <int N, typename R>
 KF_D const FiltParams<N, R> &seg_params(const OneSeq<N, R> &q, const SegCursor &) { return q.prm; }
 template <int N, typename R>
-KF_D const FiltParams<N, R> &seg_params(const ManySeq<N, R> &q, const SegCursor &c) { return q.prm[c.s]; }
+KF_D const FiltParams<N, R> &seg_params(const ManySeq<N, R> &q, const SegCursor &c) { return q.prm[__ldg(q.model_of + c.s)]; }
 
 template <int N, typename R>
 KF_HD int64_t seq_total(const OneSeq<N, R> &q) { return q.T; }

@@ -38,6 +38,7 @@ struct DlbCtl {
     void *incl;            // [ntiles][Carry::SIZE]
     double *ll_part;       // [ntiles] per-tile log-likelihood partial sums
     double *ll_out;        // final log-likelihood (nullable)
+    double *ll_step;       // per-step log-likelihood terms [total] (nullable; batched calls)
     int *status;           // device status word
     int64_t timeout_ns;    // bound of every wait
     int ntiles;
@@ -400,7 +401,9 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
                 R *o1 = obuf[0] ? stage_rec<C, (P::O1 ? P::O1 : 1), R>(obuf[0], lane, slot) : nullptr;
                 R *o2 = obuf[1] ? stage_rec<C, (P::O2 ? P::O2 : 1), R>(obuf[1], lane, slot) : nullptr;
                 R *o3 = obuf[2] ? stage_rec<C, (P::O3 ? P::O3 : 1), R>(obuf[2], lane, slot) : nullptr;
-                ll += P::step_at(args, p, cur, c, in, o1, o2, o3);
+                const double l = P::step_at(args, p, cur, c, in, o1, o2, o3);
+                ll += l;
+                if (ctl.ll_step) ctl.ll_step[gidx<P>(total, p)] = l;
             }
             __syncwarp();
             const int64_t gs = seg_first<P, C>(total, start + ch * C);
@@ -442,6 +445,24 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
             }
         }
     }
+}
+
+}  // namespace kfs
+
+namespace kfs {
+
+// Per-sequence log-likelihood of a batch: one warp per sequence sums its
+// per-step terms in a fixed order (lane-strided partial sums, then a fixed
+// shuffle tree), so the result does not depend on scheduling.
+static __global__ void segmented_ll_kernel(const double *ll_step, const int64_t *offsets, int nseg, double *ll_out) {
+    const int warp = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (warp >= nseg) return;
+    const int64_t b = offsets[warp], e = offsets[warp + 1];
+    double s = 0.0;
+    for (int64_t i = b + lane; i < e; i += 32) s += ll_step[i];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
+    if (lane == 0) ll_out[warp] = s;
 }
 
 }  // namespace kfs
