@@ -149,6 +149,37 @@ kf_status_t kf_batch_smooth(kf_op_t op, const kf_model_t *models, int nmodels, c
                             int nseq, const int64_t *offsets, const void *y, kf_precision_t prec, void *m_out,
                             void *P_out, double *loglik, void *workspace, void *stream);
 
+/* Continuous-batching server.  A scheduler thread owns one device arena of
+ * budget_bytes (allocated once, here) and max_inflight CUDA streams on the
+ * device current at creation.  Submitted jobs wait in a FIFO queue; whenever
+ * a stream is free, the oldest job and the following queued jobs of the
+ * same class (op, nx, ny, precision) that fit in the free arena space form
+ * one batch of at most max_batch_steps time steps, run as one segmented
+ * scan (kf_batch_smooth).  Jobs that arrive while batches run are admitted
+ * as streams and memory free up, so their work overlaps on the device.
+ *   - kf_server_submit: host buffers y [T][ny], and outputs m_host
+ *     [T][nx], P_host [T][nx][nx], loglik_host (1 double), each may be NULL
+ *     except y, in the working precision; they must stay valid until the job
+ *     is done.  Page-locked buffers let copies overlap the kernels; pageable
+ *     ones are correct but serialise the scheduler.  The model is copied.
+ *     A job larger than the whole budget returns KF_ERR_BUDGET.
+ *   - kf_server_poll: *done = 1 once the results are in the host buffers;
+ *     info, when not NULL, receives {submit time, batch start time, done
+ *     time (s, steady clock), batch index}.  Returns the job's status once
+ *     done, KF_ERR_BUSY for an unknown id.
+ *   - kf_server_wait: blocks until the job is done (KF_ERR_TIMEOUT after
+ *     timeout_s seconds).  kf_server_release forgets a done job.
+ *   - kf_server_destroy: finishes the queued and running jobs, then frees
+ *     the arena and streams. */
+typedef struct kf_server kf_server_t;
+kf_status_t kf_server_create(size_t budget_bytes, int max_inflight, int64_t max_batch_steps, kf_server_t **out);
+kf_status_t kf_server_submit(kf_server_t *srv, kf_op_t op, const kf_model_t *model, int64_t T, const void *y_host,
+                             kf_precision_t prec, void *m_host, void *P_host, double *loglik_host, int64_t *job_id);
+kf_status_t kf_server_poll(kf_server_t *srv, int64_t job_id, int *done, double *info);
+kf_status_t kf_server_wait(kf_server_t *srv, int64_t job_id, double timeout_s);
+kf_status_t kf_server_release(kf_server_t *srv, int64_t job_id);
+kf_status_t kf_server_destroy(kf_server_t *srv);
+
 /* RTS smoother that allocates no device memory.
  *
  * The paper has no counterpart: this is a deployment variant of

@@ -82,6 +82,15 @@ def lib():
         L.kf_batch_smooth.restype = ctypes.c_int
         L.kf_batch_workspace_size.argtypes = [i, i, i, i64, i, i, i, i]
         L.kf_batch_workspace_size.restype = ctypes.c_size_t
+        L.kf_server_create.argtypes = [ctypes.c_size_t, i, i64, ctypes.POINTER(vp)]
+        L.kf_server_submit.argtypes = [vp, i, MP, i64, vp, i, vp, vp, vp, ctypes.POINTER(i64)]
+        L.kf_server_poll.argtypes = [vp, i64, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double)]
+        L.kf_server_wait.argtypes = [vp, i64, ctypes.c_double]
+        L.kf_server_release.argtypes = [vp, i64]
+        L.kf_server_destroy.argtypes = [vp]
+        for f in ("kf_server_create", "kf_server_submit", "kf_server_poll", "kf_server_wait", "kf_server_release",
+                  "kf_server_destroy"):
+            getattr(L, f).restype = ctypes.c_int
         L.kf_rts_smooth_noalloc.restype = ctypes.c_int
         L.kf_trace_phases.restype = ctypes.c_int
         _lib = L
@@ -320,3 +329,52 @@ def kf_batch_smooth(op, models, offsets, y, precision="fp32", model_of=None, m_o
                                _ptr(m_out), _ptr(P_out), _ptr(ll), _ptr(workspace), _stream(stream))
     _check(rc, "kf_batch_smooth")
     return m_out, P_out, ll
+
+
+class Server:
+    """Continuous-batching server (kf_server_* of kfscan.h).  Jobs take host
+    torch tensors (page-locked for overlap) and write results into host
+    tensors, which the caller keeps alive until the job is done."""
+
+    def __init__(self, budget_bytes=8 << 30, max_inflight=4, max_batch_steps=1 << 24):
+        self.h = ctypes.c_void_p()
+        _check(lib().kf_server_create(int(budget_bytes), int(max_inflight), int(max_batch_steps),
+                                      ctypes.byref(self.h)), "kf_server_create")
+        self._keep = {}
+
+    def submit(self, op, model, y_host, precision, m_host=None, P_host=None, ll_host=None):
+        m = _as_model(model)
+        jid = ctypes.c_int64(0)
+        rc = lib().kf_server_submit(self.h, OPS[op], ctypes.byref(m.c), int(y_host.shape[0]), _ptr(y_host),
+                                    PRECISIONS[precision], _ptr(m_host), _ptr(P_host), _ptr(ll_host),
+                                    ctypes.byref(jid))
+        _check(rc, "kf_server_submit")
+        self._keep[jid.value] = (m, y_host, m_host, P_host, ll_host)
+        return jid.value
+
+    def poll(self, jid):
+        done = ctypes.c_int(0)
+        info = (ctypes.c_double * 4)()
+        rc = lib().kf_server_poll(self.h, int(jid), ctypes.byref(done), info)
+        if done.value:
+            _check(rc, "kf_server_poll")
+        return bool(done.value), tuple(info)
+
+    def wait(self, jid, timeout_s=60.0):
+        _check(lib().kf_server_wait(self.h, int(jid), float(timeout_s)), "kf_server_wait")
+
+    def release(self, jid):
+        _check(lib().kf_server_release(self.h, int(jid)), "kf_server_release")
+        self._keep.pop(jid, None)
+
+    def close(self):
+        if self.h:
+            _check(lib().kf_server_destroy(self.h), "kf_server_destroy")
+            self.h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
