@@ -34,8 +34,8 @@ SM_MAX_MHZ = 2070.0
 
 
 # ------------------------------------------------------------------ work model
-# FMA counts of the operator code (kf_math.cuh), derived in the design doc, with
-# n = nx, m = ny, S = n(n+1)/2; an FMA counts 2 flops.
+# FMA counts of the operator code in kf_math.cuh, counted loop by loop, with
+# n = nx, m = ny, S = n(n+1)/2; an FMA counts 2 flops, a reciprocal 1.
 
 def lemma1_flops(n):
     S = n * (n + 1) // 2
@@ -54,16 +54,44 @@ def rts_build_flops(n):
     return 2 * fma + (S - n) + 2 * n * n + 2 * n
 
 
+def lemma1_lr_flops(n, m):
+    """Lemma 1 with a fresh right operand whose J has rank m (Woodbury form)."""
+    S, Sm = n * (n + 1) // 2, m * (m + 1) // 2
+    fma = (m * n * n + Sm * n + m * n * m + S * m + m * n * n + m * n * m + n * n * m + m * n + m * m + n * (m + n)
+           + n * m + 2 * n ** 3 + n * n + S * n + n * n + n * n * m + S * n)
+    inv = {1: 2, 2: 8}.get(m, 4 * m ** 3)
+    return 2 * fma + inv
+
+
+def apply_lr_flops(n, m, loglik=True):
+    """(b, C) half of Lemma 1 for a fresh element (Woodbury form)."""
+    S, Sm = n * (n + 1) // 2, m * (m + 1) // 2
+    fma = m * n * n + Sm * n + m * n * m + S * m + m * n + m * m + n * (m + n) + n ** 3 + n + S * n
+    inv = {1: 2, 2: 8}.get(m, 4 * m ** 3)
+    f = 2 * fma + inv
+    if loglik:
+        f += 2 * (m * (m + 1) // 2 + m + m * m) + 10
+    return f
+
+
 def filter_step_flops(n, m, loglik=True):
-    # a work-efficient scan applies the operator ~2 times per element
-    f = 2 * lemma1_flops(n) + 4 * n * m
+    """Per time step of the filter scan as run: one fold of a fresh element
+    into the thread aggregate and one carry application (both in the rank-m
+    form when m = n/2), plus building (b_k, eta_k)."""
+    if 2 * m == n:
+        return lemma1_lr_flops(n, m) + apply_lr_flops(n, m, loglik) + 4 * n * m
+    f = lemma1_flops(n) + lemma1_flops(n) // 2 + 4 * n * m
     if loglik:
         f += 2 * (m * n + m * m + m + 2 * n * n + n) + n
     return f
 
 
 def rts_step_flops(n):
-    return 2 * lemma2_flops(n) + rts_build_flops(n)
+    """Per time step of the RTS scan as run: build (E, g, L), one Lemma 2
+    fold and one carry application."""
+    S = n * (n + 1) // 2
+    apply = 2 * (n ** 3 + S * n + n * n)
+    return lemma2_flops(n) + apply + rts_build_flops(n)
 
 
 def step_bytes(n, m, w):
@@ -190,6 +218,235 @@ def cpu_baseline(args):
                       "%.1f s on one host core" % (done // Ts, Ts, dt)}
 
 
+
+# ------------------------------------------------------------------ other configurations
+
+def _timed(fn, reps=12, drop=2):
+    """Median of the last reps-drop CUDA-event timings (the paper's protocol:
+    12 runs, the first 2 dropped, median of the rest)."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts[drop:]))
+
+
+def workload_sweep(args):
+    """T = 2^10 .. 2^22 on the tracking model, RTS smoother, every scan
+    algorithm, FP32 and FP64 (smoothed steps/s)."""
+    import torch
+    import paper_2511_10363_gb300 as kf
+    model = W.cv_model()
+    mdl = kf.Model(model)
+    out = {}
+    Tmax = 1 << 22
+    y64 = W.simulate(model, Tmax, seed=3)
+    for prec in ("fp32", "fp64"):
+        dt = kf.dtype_of(prec)
+        yall = torch.tensor(y64, dtype=dt, device="cuda")
+        out[prec] = {}
+        for scan in ("dlb", "ladner_fischer", "blelloch", "hillis_steele"):
+            row = {}
+            for e in range(10, 23):
+                T = 1 << e
+                y = yall[:T].contiguous()
+                ms = torch.empty((T, 4), dtype=dt, device="cuda")
+                Ps = torch.empty((T, 4, 4), dtype=dt, device="cuda")
+                ws = torch.empty(kf.kf_workspace_size("rts", 4, 2, T, prec, scan), dtype=torch.uint8, device="cuda")
+                ms_ = _timed(lambda: kf.kf_rts_smooth(mdl, y, prec, scan, ms_out=ms, Ps_out=Ps, workspace=ws))
+                assert kf.kf_sync_status() == 0
+                row[T] = {"ms": ms_, "steps_per_s": T / (ms_ * 1e-3)}
+                del ws
+            out[prec][scan] = row
+    print(json.dumps({"workload": "sweep", "metric": "smoothed steps/s", "unit": "smoothed steps/s",
+                      "model": "2D constant-velocity tracking nx=4 ny=2", "op": "rts (filter + smoother)",
+                      "timing": "median of 10 after 2 dropped runs (CUDA events)", "results": out}))
+
+
+def errors_vs_reference(m, P, ll, mref, Pref, llref):
+    """Per-output errors: normwise per step (max over steps) and elementwise
+    with an absolute floor of 1e-12 * max |x|."""
+    scale = np.maximum(np.linalg.norm(mref, axis=1), np.sqrt(np.abs(np.trace(Pref, axis1=1, axis2=2))))
+
+    def elem(a, b):
+        return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-12 * np.max(np.abs(b)))))
+    return {"mean_normwise": float(np.max(np.linalg.norm(m - mref, axis=1) / scale)),
+            "cov_normwise": float(np.max(np.linalg.norm(P - Pref, axis=(1, 2)) / np.linalg.norm(Pref, axis=(1, 2)))),
+            "mean_elementwise": elem(m, mref), "cov_elementwise": elem(P, Pref),
+            "loglik_relative": abs(ll - llref) / max(1.0, abs(llref))}
+
+
+def workload_mixed(args):
+    """Random stable LGSSM nx=8 ny=4, T=2^18: FP32 with FP64 (I + C J)
+    solves vs full FP64 vs FP32.  Errors of each output are taken against
+    this library's FP64 result on the same FP32-representable inputs (the
+    FP64 path itself is held to 1e-9 of the oracle by the parity tests)."""
+    import torch
+    import paper_2511_10363_gb300 as kf
+    model = W.random_stable_model(8, 4, seed=0)
+    T = 1 << 18
+    y = W.simulate(model, T, seed=4).astype(np.float32).astype(np.float64)
+    res, ref = {}, None
+    for prec in ("fp64", "fp32_fp64solve", "fp32"):
+        dt = kf.dtype_of(prec)
+        yt = torch.tensor(y, dtype=dt, device="cuda")
+        m_, P_, l_ = kf.kf_rts_smooth(model, yt, prec, "dlb", loglik=True)
+        t = _timed(lambda: kf.kf_rts_smooth(model, yt, prec, "dlb", loglik=True))
+        assert kf.kf_sync_status() == 0
+        out = (m_.double().cpu().numpy(), P_.double().cpu().numpy(), float(l_.item()))
+        if ref is None:
+            ref = out
+        res[prec] = {"ms": t, "steps_per_s": T / (t * 1e-3), "errors_vs_fp64": errors_vs_reference(*out, *ref)}
+    print(json.dumps({"workload": "mixed", "metric": "smoothed steps/s", "unit": "smoothed steps/s",
+                      "model": "random stable LGSSM nx=8 ny=4 (F = 0.99 Q-factor, Q = 0.1 I, R = 0.5 I)", "T": T,
+                      "results": res}))
+
+
+def workload_batch(args):
+    """4096 tracking sequences, T log-uniform in [64, 65536], RTS smoother:
+    one segmented scan over the whole batch vs one kf_rts_smooth call per
+    sequence on one stream."""
+    import torch
+    import paper_2511_10363_gb300 as kf
+    model = W.cv_model()
+    lengths = W.loguniform_lengths(4096, 64, 65536, seed=4)
+    y, offs = W.ragged_batch(model, lengths, seed=5)
+    total = int(offs[-1])
+    res = {}
+    for prec in ("fp32", "fp32_fp64solve"):
+        dt = kf.dtype_of(prec)
+        yt = torch.tensor(y, dtype=dt, device="cuda")
+        m = torch.empty((total, 4), dtype=dt, device="cuda")
+        P = torch.empty((total, 4, 4), dtype=dt, device="cuda")
+        ws = torch.empty(kf.kf_batch_workspace_size("rts", 4, 2, total, len(lengths), 1, prec), dtype=torch.uint8,
+                         device="cuda")
+        run = lambda: kf.kf_batch_smooth("rts", model, offs, yt, prec, m_out=m, P_out=P, loglik=True, workspace=ws)
+        tb = _timed(run)
+        assert kf.kf_sync_status() == 0
+        # one launch per sequence, back to back; completion time of each
+        mdl = kf.Model(model)
+        wsp = torch.empty(kf.kf_workspace_size("rts", 4, 2, int(lengths.max()), prec, "dlb"), dtype=torch.uint8,
+                          device="cuda")
+        ys = [yt[offs[i]:offs[i + 1]] for i in range(len(lengths))]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(lengths) + 1)]
+        for rep in range(2):
+            torch.cuda.synchronize()
+            evs[0].record()
+            for i in range(len(lengths)):
+                kf.kf_rts_smooth(mdl, ys[i], prec, "dlb", ms_out=m[offs[i]:offs[i + 1]], Ps_out=P[offs[i]:offs[i + 1]],
+                                 loglik=True, workspace=wsp)
+                evs[i + 1].record()
+            torch.cuda.synchronize()
+        done = np.array([evs[0].elapsed_time(e) for e in evs[1:]])
+        res[prec] = {"batched": {"ms": tb, "steps_per_s": total / (tb * 1e-3), "latency_p50_ms": tb,
+                                 "latency_p99_ms": tb, "launches_per_pass": 1},
+                     "one_launch_per_sequence": {"ms": float(done[-1]), "steps_per_s": total / (done[-1] * 1e-3),
+                                                 "latency_p50_ms": float(np.percentile(done, 50)),
+                                                 "latency_p99_ms": float(np.percentile(done, 99))}}
+    print(json.dumps({"workload": "batch", "metric": "smoothed steps/s", "unit": "smoothed steps/s",
+                      "sequences": len(lengths), "total_steps": total,
+                      "lengths": "log-uniform in [64, 65536], seed 4", "results": res}))
+
+
+def workload_serving(args):
+    """Poisson arrivals of mixed filter / RTS / two-filter jobs, nx in
+    {2, 4, 8}, T log-uniform in [256, 2^20], FP32: the continuous-batching
+    server (8 GB budget) vs one call per request on one stream."""
+    import time as _t
+    import torch
+    import paper_2511_10363_gb300 as kf
+    rng = np.random.default_rng(8)
+    rate, duration = args.rate, args.duration
+    n = int(rate * duration)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    ops = rng.choice(["filter", "rts", "tf"], size=n)
+    nxs = rng.choice([2, 4, 8], size=n)
+    Ts = np.floor(np.exp(rng.uniform(np.log(256), np.log(1 << 20), size=n))).astype(np.int64)
+    pool_len = 1 << 20
+    models, pools = {}, {}
+    for nx in (2, 4, 8):
+        models[nx] = W.model_for_nx(nx, seed=nx)
+        yp = W.simulate(models[nx], pool_len, seed=100 + nx, nseq=4).astype(np.float32)
+        pools[nx] = torch.tensor(yp).pin_memory()
+    starts = [int(rng.integers(0, pool_len - T + 1)) for T in Ts]
+    srcs = [int(rng.integers(0, 4)) for _ in range(n)]
+    outs = {nx: torch.empty((pool_len, nx), dtype=torch.float32).pin_memory() for nx in (2, 4, 8)}
+    lls = torch.empty(n, dtype=torch.float64).pin_memory()
+
+    def job(i):
+        nx = int(nxs[i])
+        return ops[i], models[nx], pools[nx][srcs[i], starts[i]:starts[i] + Ts[i]], outs[nx][:Ts[i]]
+
+    # continuous-batching server
+    srv = kf.Server(budget_bytes=8 << 30, max_inflight=4, max_batch_steps=1 << 25)
+    for i in range(min(n, 16)):   # warm-up: load kernels of every class
+        op, mdl, y, mo = job(i)
+        srv.wait(srv.submit(op, mdl, y, "fp32", mo, None, lls[i:i + 1]), 120)
+    t0 = _t.perf_counter()
+    ids = []
+    for i in range(n):
+        while _t.perf_counter() - t0 < arrivals[i]:
+            pass
+        op, mdl, y, mo = job(i)
+        ids.append(srv.submit(op, mdl, y, "fp32", mo, None, lls[i:i + 1]))
+    lat = []
+    for jid in ids:
+        srv.wait(jid, 600)
+        _, info = srv.poll(jid)
+        lat.append(info[2] - info[0])
+    t_srv = _t.perf_counter() - t0
+    srv.close()
+    steps = int(Ts.sum())
+    # one call per request, in arrival order, on one stream
+    mdls = {nx: kf.Model(models[nx]) for nx in (2, 4, 8)}
+    ydev = {nx: torch.empty((pool_len, max(1, nx // 2)), dtype=torch.float32, device="cuda") for nx in (2, 4, 8)}
+    mdev = {nx: torch.empty((pool_len, nx), dtype=torch.float32, device="cuda") for nx in (2, 4, 8)}
+    Pdev = {nx: torch.empty((pool_len, nx, nx), dtype=torch.float32, device="cuda") for nx in (2, 4, 8)}
+    ldev = torch.empty(1, dtype=torch.float64, device="cuda")
+    ws = torch.empty(max(kf.kf_workspace_size(o, nx, max(1, nx // 2), pool_len, "fp32", "dlb")
+                         for o in ("filter", "rts", "tf") for nx in (2, 4, 8)), dtype=torch.uint8, device="cuda")
+    fns = {"filter": kf.kf_filter, "rts": kf.kf_rts_smooth, "tf": kf.kf_two_filter_smooth}
+
+    def plain(i):
+        nx = int(nxs[i])
+        T = int(Ts[i])
+        y = ydev[nx][:T]
+        y.copy_(pools[nx][srcs[i], starts[i]:starts[i] + T], non_blocking=True)
+        if ops[i] == "filter":
+            kf.kf_filter(mdls[nx], y, "fp32", "dlb", m_out=mdev[nx][:T], P_out=Pdev[nx][:T], loglik=False,
+                         workspace=ws)
+        else:
+            fns[ops[i]](mdls[nx], y, "fp32", "dlb", ms_out=mdev[nx][:T], Ps_out=Pdev[nx][:T], workspace=ws)
+        outs[nx][:T].copy_(mdev[nx][:T], non_blocking=True)
+        torch.cuda.synchronize()
+
+    for i in range(min(n, 16)):
+        plain(i)
+    t0 = _t.perf_counter()
+    plat = []
+    for i in range(n):
+        while _t.perf_counter() - t0 < arrivals[i]:
+            pass
+        plain(i)
+        plat.append(_t.perf_counter() - t0 - arrivals[i])
+    t_plain = _t.perf_counter() - t0
+    print(json.dumps({
+        "workload": "serving", "metric": "smoothed steps/s", "unit": "smoothed steps/s",
+        "requests": n, "rate_per_s": rate, "arrival_window_s": duration, "total_steps": steps,
+        "mix": "filter/rts/tf uniform, nx uniform in {2,4,8} (ny = nx/2), T log-uniform in [256, 2^20], FP32",
+        "server": {"steps_per_s": steps / t_srv, "wall_s": t_srv, "latency_p50_ms": 1e3 * float(np.median(lat)),
+                   "latency_p99_ms": 1e3 * float(np.percentile(lat, 99)), "budget_bytes": 8 << 30,
+                   "streams": 4},
+        "one_call_per_request": {"steps_per_s": steps / t_plain, "wall_s": t_plain,
+                                 "latency_p50_ms": 1e3 * float(np.median(plat)),
+                                 "latency_p99_ms": 1e3 * float(np.percentile(plat, 99))}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,6 +458,10 @@ def main():
     ap.add_argument("--scan", default="dlb")
     ap.add_argument("--T", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "sweep", "mixed", "batch", "serving"],
+                    help="single: the headline line (default); the others print their own line")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--duration", type=float, default=2.0, help="serving: arrival window (s)")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up and timed steps only (no soak, end-to-end pass, CPU baseline or FMA probe): "
                          "the form run under ncu")
@@ -213,6 +474,14 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "single":
+        import torch
+        from paper_2511_10363_gb300 import build as kbuild
+        torch.cuda.set_device(local)
+        kbuild.build()
+        {"sweep": workload_sweep, "mixed": workload_mixed, "batch": workload_batch,
+         "serving": workload_serving}[args.workload](args)
         return
 
     import torch

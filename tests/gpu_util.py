@@ -4,9 +4,11 @@ import numpy as np
 
 import oracle
 
-# Tolerances on per-step normwise relative errors ("Parity"):
+# Tolerances on per-step normwise relative errors:
 #   means:       |dm_k| / max(|m_k|, sqrt(tr P_k))
 #   covariances: |dP_k|_F / |P_k|_F
+# Elementwise relative error is ill-posed for entries near zero (cross
+# covariances, velocities near zero), so the gate is normwise per step.
 TOL = {"fp64": 1e-9, "fp32": 1e-4, "fp32_fp64solve": 1e-4}
 
 
