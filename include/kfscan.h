@@ -279,10 +279,13 @@ kf_status_t kf_timing_read(kf_kernel_t kind, int64_t *launches, double *total_ms
 
 /* Phase trace (diagnostics).  While a buffer is set for a decoupled
  * look-back scan kind (FILTER/RTS/TF_SCAN), every later launch of that scan
- * writes, for each tile t < capacity_tiles, five %globaltimer stamps (ns) to
- * device_buffer[8 t .. 8 t + 4]: CTA start, end of the thread fold + warp
- * scan, aggregate published, look-back done, end of the extraction pass.
- * device_buffer is a caller-owned DEVICE buffer of 8 * capacity_tiles
+ * writes, for each tile t < capacity_tiles, %globaltimer stamps (ns) to
+ * device_buffer[16 t + i]: i = 0 CTA start, 1 end of the thread fold + warp
+ * scan, 2 aggregate published, 3 look-back done, 4 end of the extraction
+ * pass; for tiles > 0 also 5 predecessor flags seen, 6 predecessor folds
+ * done, 7 warp trees done, 8 warp-0 tree done, 9 inclusive carry loaded,
+ * 10 exclusive carry applied, 11 inclusive carry computed, 12 published.
+ * device_buffer is a caller-owned DEVICE buffer of 16 * capacity_tiles
  * uint64; NULL switches the trace off. */
 kf_status_t kf_trace_phases(kf_kernel_t kind, void *device_buffer, int capacity_tiles);
 

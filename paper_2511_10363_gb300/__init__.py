@@ -274,8 +274,8 @@ def rts_smooth_host(model, y_host, precision, scan, ms_host, Ps_host, ll_host=No
 
 def kf_trace_phases(kind, buf=None):
     """Set (or clear, buf=None) the phase-trace device buffer (int64 tensor
-    of 8 * capacity entries) of a look-back scan kind."""
-    cap = 0 if buf is None else buf.numel() // 8
+    of 16 * capacity entries) of a look-back scan kind."""
+    cap = 0 if buf is None else buf.numel() // 16
     _check(lib().kf_trace_phases(int(kind), _ptr(buf), cap), "kf_trace_phases")
 
 

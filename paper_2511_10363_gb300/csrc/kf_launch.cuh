@@ -43,6 +43,7 @@ void to_params(const HostModel &h, FiltParams<N, R> &p) {
     }
     p.llc = h.llc;
     p.llc1 = h.llc1;
+    p.llc_r = R(h.llc);
     for (int j = 0; j < h.m; ++j) {
         for (int k = 0; k < n; ++k) p.U[j * N + k] = R(h.U[j * n + k]);
         for (int k = 0; k < h.m; ++k) p.Linv[j * MAXNY + k] = R(h.Linv[j * h.m + k]);

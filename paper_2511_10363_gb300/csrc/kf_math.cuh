@@ -160,6 +160,7 @@ struct FiltParams {
     R S1inv[MAXNY * MAXNY];       //   S_1^{-1}, S_1 = H P_{1|0} H^T + R
     R Hx1[MAXNY];                 //   H xbar_{1|0}
     double llc, llc1;             //   log det S + m log 2 pi,  log det S_1 + m log 2 pi
+    R llc_r;                      //   llc in the working precision
     R F[NN], Q[S];                // RTS elements, Eq. prts_init1
     R U[MAXNY * N];               // J = U^T U, U = L^{-1} H F with S = L L^T (low-rank path)
     R Linv[MAXNY * MAXNY];        //   L^{-1} (lower triangular)
@@ -660,8 +661,8 @@ KF_D void spd_inverse(const T *Pp, T *W, T &logdet) {
 // G = U C (M x N), W = (I_M + G U^T)^{-1} (packed M x M) and log det of it.
 // MODE 1 forms I + G U^T and inverts it in FP64, then applies one step of
 // iterative refinement W <- W + W (I - P W) in FP64.
-template <int N, int M, typename R, int MODE>
-KF_D void lowrank_core(const R *C, const R *U, R G[M * N], R Wp[M * (M + 1) / 2], double &logdet) {
+template <int N, int M, typename R, int MODE, typename LD>
+KF_D void lowrank_core(const R *C, const R *U, R G[M * N], R Wp[M * (M + 1) / 2], LD &logdet) {
 #pragma unroll
     for (int i = 0; i < M; ++i)
 #pragma unroll
@@ -684,7 +685,7 @@ KF_D void lowrank_core(const R *C, const R *U, R G[M * N], R Wp[M * (M + 1) / 2]
             }
         R ld;
         spd_inverse<M, R>(Pp, Wp, ld);
-        logdet = double(ld);
+        logdet = LD(ld);
     } else {
         double Pp[M * (M + 1) / 2], Wd[M * (M + 1) / 2];
 #pragma unroll
@@ -718,7 +719,7 @@ KF_D void lowrank_core(const R *C, const R *U, R G[M * N], R Wp[M * (M + 1) / 2]
                 for (int k = 0; k < M; ++k) t += Wd[si(M, i, k)] * E[k * M + j];
                 Wp[su(M, i, j)] = R(t);
             }
-        logdet = ld;
+        logdet = LD(ld);
     }
 }
 
@@ -732,8 +733,8 @@ KF_D void lemma1_lr_parts(const FElem<N, R> &ei, const R *Aj, const R *bj, const
     constexpr int SM = M * (M + 1) / 2;
     const R *Ai = ei.v + E::oA, *bi = ei.v + E::ob, *Ci = ei.v + E::oC, *etai = ei.v + E::oe, *Ji = ei.v + E::oJ;
     R G[M * N], W[SM];
-    double ld;
-    lowrank_core<N, M, R, MODE>(Ci, U, G, W, ld);
+    R ld;
+    lowrank_core<N, M, R, MODE, R>(Ci, U, G, W, ld);
     // WG = W G; D = C_i - G^T W G
     R WG[M * N];
 #pragma unroll
@@ -895,12 +896,12 @@ KF_D void lemma1_lr(const FElem<N, R> &ei, const FElem<N, R> &ej, const R *U, FE
 // which give log N(y_k; H F b, S_k) since S_k = L (I_m + U C U^T) L^T.
 template <int N, int M, typename R, int MODE, bool LL>
 KF_D void apply_fwd_lr_parts(FwdCarry<N, R> &c, const R *Aj, const R *bj, const R *Cj, const R *etaj, const R *U,
-                             const R *ytil, R *quad, double *logdet) {
+                             const R *ytil, R *quad, R *logdet) {
     using CT = FwdCarry<N, R>;
     const R *b = c.v + CT::ob, *C = c.v + CT::oC;
     R G[M * N], W[M * (M + 1) / 2];
-    double ld;
-    lowrank_core<N, M, R, MODE>(C, U, G, W, ld);
+    R ld;
+    lowrank_core<N, M, R, MODE, R>(C, U, G, W, ld);
     R WG[M * N];
 #pragma unroll
     for (int i = 0; i < M; ++i)
@@ -986,8 +987,7 @@ KF_D void apply_fwd_lr_parts(FwdCarry<N, R> &c, const R *Aj, const R *bj, const 
 }
 
 template <int N, int M, typename R, int MODE, bool LL>
-KF_D void apply_fwd_lr(FwdCarry<N, R> &c, const FElem<N, R> &ej, const R *U, const R *ytil, R *quad,
-                       double *logdet) {
+KF_D void apply_fwd_lr(FwdCarry<N, R> &c, const FElem<N, R> &ej, const R *U, const R *ytil, R *quad, R *logdet) {
     using E = FElem<N, R>;
     apply_fwd_lr_parts<N, M, R, MODE, LL>(c, ej.v + E::oA, ej.v + E::ob, ej.v + E::oC, ej.v + E::oe, U, ytil, quad,
                                           logdet);
@@ -1174,7 +1174,7 @@ KF_D void build_rts_elem(const FiltParams<N, R> &P, bool last, const R *x, const
             if (i == j) {
                 const R d = sqrt(s);
                 L[i * (i + 1) / 2 + i] = d;
-                dinv[i] = R(1) / d;
+                dinv[i] = recip(d);
             } else {
                 L[i * (i + 1) / 2 + j] = s * dinv[j];
             }

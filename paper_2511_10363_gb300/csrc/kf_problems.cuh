@@ -137,11 +137,11 @@ KF_D void op_lemma1_lr(const FElem<N, R> &a, const FElem<N, R> &b, const R *U, F
 }
 template <int N, int M, typename R, int MODE, bool LL>
 __device__ __noinline__ void apply_fwd_lr_ool(FwdCarry<N, R> &c, const FElem<N, R> &e, const R *U, const R *yt, R *q,
-                                              double *ld) {
+                                              R *ld) {
     apply_fwd_lr<N, M, R, MODE, LL>(c, e, U, yt, q, ld);
 }
 template <int N, int M, typename R, int MODE, bool LL>
-KF_D void op_apply_fwd_lr(FwdCarry<N, R> &c, const FElem<N, R> &e, const R *U, const R *yt, R *q, double *ld) {
+KF_D void op_apply_fwd_lr(FwdCarry<N, R> &c, const FElem<N, R> &e, const R *U, const R *yt, R *q, R *ld) {
     if constexpr (N >= 8) apply_fwd_lr_ool<N, M, R, MODE, LL>(c, e, U, yt, q, ld);
     else apply_fwd_lr<N, M, R, MODE, LL>(c, e, U, yt, q, ld);
 }
@@ -308,8 +308,7 @@ struct FilterFwd {
                         for (int k = 0; k <= i; ++k) s += P.Linv[i * MAXNY + k] * yv[k];
                         yt[i] = s;
                     }
-                    R q;
-                    double ld;
+                    R q, ld;
                     if constexpr (N >= 8) {
                         Elem e;
                         build_filter_elem<N, R>(P, 2, yv, e);
@@ -317,7 +316,8 @@ struct FilterFwd {
                     } else {
                         apply_fwd_lr_parts<N, LR, R, MODE, true>(c, P.A, b, P.C, eta, P.U, yt, &q, &ld);
                     }
-                    ll = -0.5 * (double(q) + ld + P.llc);
+                    // the per-step term in the working precision; FP64 only accumulates
+                    ll = double(R(-0.5) * (q + ld + P.llc_r));
                 } else {
                     if constexpr (N >= 8) {
                         Elem e;
@@ -367,10 +367,9 @@ struct FilterFwd {
                 for (int k = 0; k <= i; ++k) s += P.Linv[i * MAXNY + k] * yk[k];
                 yt[i] = s;
             }
-            R q;
-            double ld;
+            R q, ld;
             op_apply_fwd_lr<N, LR, R, MODE, true>(c, e, P.U, yt, &q, &ld);
-            ll = -0.5 * (double(q) + ld + P.llc);
+            ll = double(R(-0.5) * (q + ld + P.llc_r));
         } else {
             const R *b = c.v + Carry::ob;
             R v[MAXNY];

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
     __syncthreads();
     const int tile = s_tile;
     if (tile >= ctl.ntiles || tile == ctl.inject_skip_tile) return;
-    uint64_t *const trace = (ctl.trace && tile < ctl.trace_cap && threadIdx.x == 0) ? ctl.trace + 8 * tile : nullptr;
+    uint64_t *const trace = (ctl.trace && tile < ctl.trace_cap && threadIdx.x == 0) ? ctl.trace + 16 * tile : nullptr;
     if (trace) trace[0] = global_ns();
     const int64_t total = P::total(args);
     const int64_t start = (int64_t(tile) * THREADS + tid) * ctl.K;
@@ -335,14 +335,18 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
                     y = t;
                 }
             }
+            if (trace) trace[8] = global_ns();
             if (qstar >= 0) load_cg(tc, static_cast<const R *>(ctl.incl) + int64_t(qstar) * CS);
+            if (trace) trace[9] = global_ns();
             P::apply(tc, y);
+            if (trace) trace[10] = global_ns();
         }
     }
     // ---- 5. publish the inclusive carry
     if (warp == 0) {
         Carry inc = tc;
         P::apply(inc, tagg);
+        if (trace) trace[11] = global_ns();
         if (lane == 0) {
 #pragma unroll
             for (int i = 0; i < CS; ++i) s_carry[i] = tc.v[i];
@@ -351,6 +355,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
             for (int i = 0; i < CS; ++i) dst[i] = inc.v[i];
             __threadfence();
             st_release(ctl.flags + tile, 2);
+            if (trace) trace[12] = global_ns();
         }
     }
     __syncthreads();
@@ -392,6 +397,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
                 }
                 __syncwarp();
             }
+            R llc = 0;   // log-likelihood terms of this chunk, summed in the working precision
 #pragma unroll 1
             for (int cc = 0; cc < C; ++cc) {
                 const int64_t p = start + ch * C + cc;
@@ -402,9 +408,10 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
                 R *o2 = obuf[1] ? stage_rec<C, (P::O2 ? P::O2 : 1), R>(obuf[1], lane, slot) : nullptr;
                 R *o3 = obuf[2] ? stage_rec<C, (P::O3 ? P::O3 : 1), R>(obuf[2], lane, slot) : nullptr;
                 const double l = P::step_at(args, p, cur, c, in, o1, o2, o3);
-                ll += l;
+                llc += R(l);
                 if (ctl.ll_step) ctl.ll_step[gidx<P>(total, p)] = l;
             }
+            ll += double(llc);   // FP64 accumulation, once per chunk of at most C steps
             __syncwarp();
             const int64_t gs = seg_first<P, C>(total, start + ch * C);
             if constexpr (P::O1 > 0) if (obuf[0]) stage_store<C, P::O1>(oarr[0], gs, lo, hi, obuf[0], lane);
