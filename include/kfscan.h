@@ -101,7 +101,9 @@ const char *kf_version(void);
 typedef enum { KF_OP_FILTER = 0, KF_OP_RTS = 1, KF_OP_TWO_FILTER = 2 } kf_op_t;
 
 /* Bytes of device workspace needed by one call of the given operation on
- * total_steps time steps (the sum of the lengths for a batched call). */
+ * total_steps time steps (the sum of the lengths for a batched call).
+ * For KF_SCAN_AUTO it is the larger of the look-back and level-scan needs,
+ * so it covers whichever algorithm a tuning-table entry selects. */
 size_t kf_workspace_size(kf_op_t op, int nx, int ny, int64_t total_steps, kf_precision_t prec,
                          kf_scan_t scan);
 
@@ -288,6 +290,27 @@ kf_status_t kf_timing_read(kf_kernel_t kind, int64_t *launches, double *total_ms
  * device_buffer is a caller-owned DEVICE buffer of 16 * capacity_tiles
  * uint64; NULL switches the trace off. */
 kf_status_t kf_trace_phases(kf_kernel_t kind, void *device_buffer, int capacity_tiles);
+
+/* Autotuner.  kf_autotune times the candidate launch configurations of one
+ * call -- the decoupled look-back scan with 128 (and, for nx = 4 in FP32,
+ * 256) threads per CTA, 1, 2, 4 or all warps in the look-back and three
+ * tile sizes, and the in-place Ladner-Fischer level scan -- on the caller's
+ * model, data and output buffers (median of reps runs each, after one
+ * warm-up; outputs are overwritten), and records the fastest for
+ * (op, nx, ny, precision, floor(log2 T)).  Later calls with KF_SCAN_AUTO and
+ * that key use the recorded configuration, unless KF_OPT_THREADS,
+ * KF_OPT_LOOKBACK_WARPS or KF_OPT_POSITIONS_PER_THREAD is set.  Synchronous;
+ * kf_timing_enable must be off; workspace is null or at least
+ * kf_workspace_size(op, ..., KF_SCAN_AUTO) bytes.  kf_tuning_get reads an entry;
+ * kf_tuning_save / kf_tuning_load write / merge a text file of entries;
+ * kf_tuning_clear empties the table. */
+kf_status_t kf_autotune(kf_op_t op, const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec,
+                        void *m_out, void *P_out, int reps, void *workspace, void *stream);
+kf_status_t kf_tuning_get(kf_op_t op, int nx, int ny, kf_precision_t prec, int64_t T, int *scan, int *threads,
+                          int *lookback_warps, int *steps_per_thread, double *ms);
+kf_status_t kf_tuning_save(const char *path);
+kf_status_t kf_tuning_load(const char *path);
+kf_status_t kf_tuning_clear(void);
 
 /* Measures the FP32 (fp64 = 0) or FP64 (fp64 = 1) fused multiply-add
  * throughput of the current device with a kernel of independent FMA chains

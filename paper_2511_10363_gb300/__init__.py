@@ -77,6 +77,13 @@ def lib():
         L.kf_timing_read.argtypes = [i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
         L.kf_measure_fma_peak.argtypes = [i, ctypes.POINTER(ctypes.c_double)]
         L.kf_trace_phases.argtypes = [i, vp, i]
+        L.kf_autotune.argtypes = [i, MP, i64, vp, i, vp, vp, i, vp, vp]
+        IP = ctypes.POINTER(ctypes.c_int)
+        L.kf_tuning_get.argtypes = [i, i, i, i, i64, IP, IP, IP, IP, ctypes.POINTER(ctypes.c_double)]
+        L.kf_tuning_save.argtypes = [ctypes.c_char_p]
+        L.kf_tuning_load.argtypes = [ctypes.c_char_p]
+        for f in ("kf_autotune", "kf_tuning_get", "kf_tuning_save", "kf_tuning_load", "kf_tuning_clear"):
+            getattr(L, f).restype = ctypes.c_int
         L.kf_rts_smooth_noalloc.argtypes = [MP, i64, vp, i, vp, vp, vp, vp, vp]
         L.kf_batch_smooth.argtypes = [i, MP, i, vp, i, vp, vp, i, vp, vp, vp, vp, vp]
         L.kf_batch_smooth.restype = ctypes.c_int
@@ -378,3 +385,42 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+SCAN_NAMES = {1: "dlb", 2: "hillis_steele", 3: "blelloch", 4: "ladner_fischer"}
+
+
+def kf_autotune(op, model, y, precision="fp32", reps=5, workspace=None, stream=None):
+    """Time the candidate configurations of one call on these inputs and
+    record the fastest (see kfscan.h).  Returns the recorded entry."""
+    import torch
+    m, dt = _prep(model, y, precision)
+    T = y.shape[0]
+    mo = torch.empty((T, m.nx), dtype=dt, device=y.device)
+    Po = torch.empty((T, m.nx, m.nx), dtype=dt, device=y.device)
+    _check(lib().kf_autotune(OPS[op], ctypes.byref(m.c), T, _ptr(y), PRECISIONS[precision], _ptr(mo), _ptr(Po),
+                             int(reps), _ptr(workspace), _stream(stream)), "kf_autotune")
+    return kf_tuning_get(op, m.nx, m.ny, precision, T)
+
+
+def kf_tuning_get(op, nx, ny, precision, T):
+    v = [ctypes.c_int(0) for _ in range(4)]
+    ms = ctypes.c_double(0)
+    rc = lib().kf_tuning_get(OPS[op], nx, ny, PRECISIONS[precision], int(T), *[ctypes.byref(x) for x in v],
+                             ctypes.byref(ms))
+    if rc != 0:
+        return None
+    return {"scan": SCAN_NAMES[v[0].value], "threads": v[1].value, "lookback_warps": v[2].value,
+            "steps_per_thread": v[3].value, "ms": ms.value}
+
+
+def kf_tuning_save(path):
+    _check(lib().kf_tuning_save(str(path).encode()), "kf_tuning_save")
+
+
+def kf_tuning_load(path):
+    _check(lib().kf_tuning_load(str(path).encode()), "kf_tuning_load")
+
+
+def kf_tuning_clear():
+    _check(lib().kf_tuning_clear(), "kf_tuning_clear")

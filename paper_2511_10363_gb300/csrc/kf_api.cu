@@ -6,8 +6,12 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <algorithm>
+
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <vector>
 
 #include "../../include/kfscan.h"
 #include "kf_host.h"
@@ -370,6 +374,42 @@ static kf_status_t check_model(const kf_model_t *md) {
     return KF_OK;
 }
 
+// ---------------------------------------------------------------- tuning table
+
+// Best launch configuration found by kf_autotune, keyed by operation, sizes,
+// precision and floor(log2 T); applied to calls that ask for KF_SCAN_AUTO
+// while the corresponding process-wide options are at their defaults.
+struct TuneKey {
+    int op, nx, ny, prec, logT;
+    bool operator<(const TuneKey &o) const {
+        if (op != o.op) return op < o.op;
+        if (nx != o.nx) return nx < o.nx;
+        if (ny != o.ny) return ny < o.ny;
+        if (prec != o.prec) return prec < o.prec;
+        return logT < o.logT;
+    }
+};
+struct TuneCfg {
+    int scan, threads, lookback_warps, k;
+    double ms;
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneCfg> g_tune;
+
+static int floor_log2(int64_t T) {
+    int l = 0;
+    while ((int64_t(2) << l) <= T) ++l;
+    return l;
+}
+
+static bool tuned(int op, int nx, int ny, int prec, int64_t T, TuneCfg *c) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(TuneKey{op, nx, ny, prec, floor_log2(T)});
+    if (it == g_tune.end()) return false;
+    *c = it->second;
+    return true;
+}
+
 static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, kf_precision_t prec,
                        kf_scan_t scan, void *m1, void *P1, void *m2, void *P2, double *loglik, void *workspace,
                        void *stream) {
@@ -416,6 +456,13 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
     q.threads = int(g_opt[KF_OPT_THREADS].load());
     q.no_lowrank = int(g_opt[KF_OPT_GENERAL_SOLVE].load());
     q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
+    TuneCfg tc;
+    if (scan == KF_SCAN_AUTO && tuned(op, md->nx, md->ny, q.prec, T, &tc)) {
+        q.scan = tc.scan;
+        if (q.threads == 0) q.threads = tc.threads;
+        if (q.lookback_warps == 0) q.lookback_warps = tc.lookback_warps;
+        if (q.k_override == 0) q.k_override = tc.k;
+    }
     s = device_status_word(&q.status);
     KF_DBG("status word %p (%d)\n", (void *)q.status, int(s));
     if (s != KF_OK) return s;
@@ -655,8 +702,12 @@ size_t kf_workspace_size(kf_op_t op, int nx, int ny, int64_t total_steps, kf_pre
     if (op < KF_OP_FILTER || op > KF_OP_TWO_FILTER) return 0;
     if (prec != KF_FP64 && prec != KF_FP32 && prec != KF_FP32_FP64SOLVE) return 0;
     if (scan < KF_SCAN_AUTO || scan > KF_SCAN_LADNER_FISCHER) return 0;
-    const int sc = (scan == KF_SCAN_AUTO) ? KF_SCAN_DLB_I : int(scan);
-    return ws_bytes_dispatch(nx, int(op), int(prec), sc, total_steps);
+    if (scan == KF_SCAN_AUTO) {   // room for whichever algorithm the tuning table may pick
+        const size_t a = ws_bytes_dispatch(nx, int(op), int(prec), KF_SCAN_DLB_I, total_steps);
+        const size_t b = ws_bytes_dispatch(nx, int(op), int(prec), KF_SCAN_LAFI_I, total_steps);
+        return a > b ? a : b;
+    }
+    return ws_bytes_dispatch(nx, int(op), int(prec), int(scan), total_steps);
 }
 
 kf_status_t kf_filter(const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec, kf_scan_t scan,
@@ -695,6 +746,136 @@ kf_status_t kf_batch_smooth(kf_op_t op, const kf_model_t *models, int nmodels, c
 kf_status_t kf_rts_smooth_noalloc(const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec,
                                   void *ms_out, void *Ps_out, double *loglik, int *status_out, void *stream) {
     return rts_noalloc(model, T, y, prec, ms_out, Ps_out, loglik, status_out, stream);
+}
+
+
+// ---------------------------------------------------------------- autotuner
+
+kf_status_t kf_autotune(kf_op_t op, const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec,
+                        void *m_out, void *P_out, int reps, void *workspace, void *stream) {
+    if (!model || !y || !m_out || reps < 1 || reps > 1000) return KF_ERR_ARG;
+    if (op != KF_OP_FILTER && !P_out) return KF_ERR_ARG;
+    if (timing_on()) return KF_ERR_ARG;
+    const int nx = model->nx;
+    std::vector<TuneCfg> cands;
+    // level algorithms: in-place Ladner-Fischer (the best of Algs. 1-3 on this hardware)
+    cands.push_back(TuneCfg{KF_SCAN_LAFI_I, 0, 0, 0, 0});
+    const int threads_opts[2] = {128, 256};
+    for (int th : threads_opts) {
+        if (th == 256 && !(nx == 4 && prec == KF_FP32)) continue;
+        for (int lb = 1; lb <= th / 32; lb *= 2)
+            for (int kscale = 0; kscale < 3; ++kscale) {
+                // k = 0: one wave of resident tiles; otherwise a fixed number of steps per thread
+                int k = 0;
+                if (kscale > 0) {
+                    int64_t per = (T + int64_t(152) * th - 1) / (int64_t(152) * th);
+                    k = int(kscale == 1 ? (per + 1) / 2 : per * 2);
+                    if (k < 1) k = 1;
+                }
+                cands.push_back(TuneCfg{KF_SCAN_DLB_I, th, lb, k, 0});
+            }
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KF_ERR_CUDA;
+    const int64_t saved[4] = {g_opt[KF_OPT_THREADS].load(), g_opt[KF_OPT_LOOKBACK_WARPS].load(),
+                              g_opt[KF_OPT_POSITIONS_PER_THREAD].load(), 0};
+    TuneCfg best{KF_SCAN_DLB_I, 0, 0, 0, 1e30};
+    kf_status_t s = KF_OK;
+    for (TuneCfg c : cands) {
+        g_opt[KF_OPT_THREADS].store(c.threads);
+        g_opt[KF_OPT_LOOKBACK_WARPS].store(c.lookback_warps);
+        g_opt[KF_OPT_POSITIONS_PER_THREAD].store(c.k);
+        const kf_scan_t sc = kf_scan_t(c.scan);
+        auto call = [&]() -> kf_status_t {
+            if (op == KF_OP_FILTER) return kf_filter(model, T, y, prec, sc, m_out, P_out, nullptr, workspace, stream);
+            if (op == KF_OP_RTS)
+                return kf_rts_smooth(model, T, y, prec, sc, m_out, P_out, nullptr, nullptr, nullptr, workspace, stream);
+            return kf_two_filter_smooth(model, T, y, prec, sc, m_out, P_out, nullptr, nullptr, nullptr, workspace,
+                                        stream);
+        };
+        s = call();   // warm-up (also loads the kernels)
+        if (s != KF_OK) break;
+        std::vector<float> ts;
+        for (int r = 0; r < reps && s == KF_OK; ++r) {
+            cudaEventRecord(e0, st);
+            s = call();
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) s = KF_ERR_CUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ts.push_back(ms);
+        }
+        if (s != KF_OK) break;
+        std::sort(ts.begin(), ts.end());
+        c.ms = ts[ts.size() / 2];
+        if (c.ms < best.ms) best = c;
+    }
+    g_opt[KF_OPT_THREADS].store(saved[0]);
+    g_opt[KF_OPT_LOOKBACK_WARPS].store(saved[1]);
+    g_opt[KF_OPT_POSITIONS_PER_THREAD].store(saved[2]);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != KF_OK) return s;
+    if (kf_sync_status(stream) != KF_OK) return KF_ERR_TIMEOUT;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[TuneKey{int(op), model->nx, model->ny, int(prec), floor_log2(T)}] = best;
+    return KF_OK;
+}
+
+kf_status_t kf_tuning_get(kf_op_t op, int nx, int ny, kf_precision_t prec, int64_t T, int *scan, int *threads,
+                          int *lookback_warps, int *steps_per_thread, double *ms) {
+    TuneCfg c;
+    if (!tuned(int(op), nx, ny, int(prec), T, &c)) return KF_ERR_ARG;
+    if (scan) *scan = c.scan;
+    if (threads) *threads = c.threads;
+    if (lookback_warps) *lookback_warps = c.lookback_warps;
+    if (steps_per_thread) *steps_per_thread = c.k;
+    if (ms) *ms = c.ms;
+    return KF_OK;
+}
+
+kf_status_t kf_tuning_save(const char *path) {
+    if (!path) return KF_ERR_ARG;
+    FILE *f = fopen(path, "w");
+    if (!f) return KF_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    fprintf(f, "# kfscan tuning: op nx ny prec log2T scan threads lookback_warps steps_per_thread ms\n");
+    for (auto &kv : g_tune)
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %.17g\n", kv.first.op, kv.first.nx, kv.first.ny, kv.first.prec,
+                kv.first.logT, kv.second.scan, kv.second.threads, kv.second.lookback_warps, kv.second.k, kv.second.ms);
+    fclose(f);
+    return KF_OK;
+}
+
+kf_status_t kf_tuning_load(const char *path) {
+    if (!path) return KF_ERR_ARG;
+    FILE *f = fopen(path, "r");
+    if (!f) return KF_ERR_ARG;
+    char line[256];
+    std::map<TuneKey, TuneCfg> t;
+    while (fgets(line, sizeof(line), f)) {
+        if (line[0] == '#') continue;
+        TuneKey k;
+        TuneCfg c;
+        if (sscanf(line, "%d %d %d %d %d %d %d %d %d %lf", &k.op, &k.nx, &k.ny, &k.prec, &k.logT, &c.scan, &c.threads,
+                   &c.lookback_warps, &c.k, &c.ms) == 10) {
+            if (c.scan < KF_SCAN_DLB_I || c.scan > KF_SCAN_LAFI_I || (c.threads != 0 && c.threads != 128 &&
+                                                                     c.threads != 256))
+                continue;
+            t[k] = c;
+        }
+    }
+    fclose(f);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &kv : t) g_tune[kv.first] = kv.second;
+    return KF_OK;
+}
+
+kf_status_t kf_tuning_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+    return KF_OK;
 }
 
 kf_status_t kf_sync_status(void *stream) {

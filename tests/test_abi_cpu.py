@@ -103,3 +103,36 @@ def test_options(lib):
     kf.kf_set_option("wait_timeout_ns", 5 * 10 ** 8)
     assert kf.kf_get_option("wait_timeout_ns") == 5 * 10 ** 8
     kf.kf_set_option("wait_timeout_ns", 10 ** 9)
+
+
+def test_tuning_table_file(lib, tmp_path):
+    """The tuning table is host state: load, query, save and clear need no GPU.
+    Malformed or out-of-range lines are skipped."""
+    kf.kf_tuning_clear()
+    src = tmp_path / "in.txt"
+    src.write_text("# comment\n"
+                   "1 4 2 1 20 1 256 2 0 0.25\n"      # rts, nx 4, ny 2, fp32, T in [2^20, 2^21)
+                   "0 8 4 0 12 4 0 0 0 1.5\n"         # filter, nx 8, fp64, level scan
+                   "1 4 2 1 19 9 128 1 0 0.1\n"       # unknown scan: skipped
+                   "1 4 2 1 18 1 100 1 0 0.1\n"       # bad thread count: skipped
+                   "garbage\n")
+    kf.kf_tuning_load(src)
+    e = kf.kf_tuning_get("rts", 4, 2, "fp32", (1 << 20) + 5)
+    assert e == {"scan": "dlb", "threads": 256, "lookback_warps": 2, "steps_per_thread": 0, "ms": 0.25}
+    assert kf.kf_tuning_get("rts", 4, 2, "fp32", (1 << 20) - 1) is None
+    assert kf.kf_tuning_get("filter", 8, 4, "fp64", 5000)["scan"] == "ladner_fischer"
+    assert kf.kf_tuning_get("rts", 4, 2, "fp32", 1 << 19) is None
+    assert kf.kf_tuning_get("rts", 4, 2, "fp32", 1 << 18) is None
+    out = tmp_path / "out.txt"
+    kf.kf_tuning_save(out)
+    kf.kf_tuning_clear()
+    assert kf.kf_tuning_get("rts", 4, 2, "fp32", 1 << 20) is None
+    kf.kf_tuning_load(out)
+    assert kf.kf_tuning_get("rts", 4, 2, "fp32", 1 << 20) == e
+    with pytest.raises(kf.KfError):
+        kf.kf_tuning_load(tmp_path / "missing.txt")
+    kf.kf_tuning_clear()
+    # the AUTO workspace covers the look-back and the level scans
+    auto = kf.kf_workspace_size("rts", 4, 2, 1 << 16, "fp32", "auto")
+    assert auto >= kf.kf_workspace_size("rts", 4, 2, 1 << 16, "fp32", "dlb")
+    assert auto >= kf.kf_workspace_size("rts", 4, 2, 1 << 16, "fp32", "ladner_fischer")
