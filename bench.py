@@ -28,6 +28,7 @@ import numpy as np  # noqa: E402
 
 import workloads as W  # noqa: E402
 
+TUNING_TABLE = os.path.join(ROOT, "paper_2511_10363_gb300", "tuning_gb300.txt")
 FP32_LANES_PER_SM = 128      # Blackwell SM: 4 SMSPs x 32 FP32 lanes
 N_SM = 152                   # GB300
 SM_MAX_MHZ = 2070.0
@@ -74,12 +75,19 @@ def apply_lr_flops(n, m, loglik=True):
     return f
 
 
+def table_fold_flops(n, m):
+    """One step of the table-driven thread fold (time-invariant model, m = n/2):
+    v = L^{-1} y - U b, b <- T1 b + T4 y, eta <- eta + T3U v."""
+    fma = m * (m + 1) // 2 + m * n + n * m + n * n + n * m
+    return 2 * fma
+
+
 def filter_step_flops(n, m, loglik=True):
-    """Per time step of the filter scan as run: one fold of a fresh element
-    into the thread aggregate and one carry application (both in the rank-m
+    """Per time step of the filter scan as run: one fold step (the fold table
+    when m = n/2, else one Lemma 1 combine) and one carry application (rank-m
     form when m = n/2), plus building (b_k, eta_k)."""
     if 2 * m == n:
-        return lemma1_lr_flops(n, m) + apply_lr_flops(n, m, loglik) + 4 * n * m
+        return table_fold_flops(n, m) + apply_lr_flops(n, m, loglik) + 4 * n * m
     f = lemma1_flops(n) + lemma1_flops(n) // 2 + 4 * n * m
     if loglik:
         f += 2 * (m * n + m * m + m + 2 * n * n + n) + n
@@ -99,6 +107,38 @@ def step_bytes(n, m, w):
     filt = (m + n + S) * w                  # read y, write filter mean + packed cov
     rts = (n + S) * w + (n + n * n) * w     # read them back, write smoothed mean + full cov
     return filt, rts
+
+
+# ------------------------------------------------------------------ DRAM traffic
+
+def kernel_source_hash():
+    """sha256 over the CUDA sources, so that a recorded ncu traffic figure is
+    used only for the kernels it was measured on."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2511_10363_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, precision, T, cfg):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    recorded under profiles/ for this kernel, workload and launch
+    configuration; None when absent or measured on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for line in open(path):
+        f = line.split()
+        if len(f) == 6 and not line.startswith("#"):
+            src, k, prec, t, c, b = f
+            if src == want and k == kernel and prec == precision and int(t) == T and c == cfg:
+                return int(b)
+    return None
 
 
 # ------------------------------------------------------------------ clocks
@@ -455,8 +495,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_fp64solve"])
     ap.add_argument("--op", default="rts", choices=["rts", "tf"])
-    ap.add_argument("--scan", default="dlb")
+    ap.add_argument("--scan", default="auto",
+                    help="auto (autotuned, default), dlb, hillis_steele, blelloch or ladner_fischer")
     ap.add_argument("--T", type=int, default=1 << 20)
+    ap.add_argument("--threads", type=int, default=0, help="fix the CTA size (with --scan dlb)")
+    ap.add_argument("--lbw", type=int, default=0, help="fix the look-back warps (with --scan dlb)")
+    ap.add_argument("--k", type=int, default=0, help="fix the time steps per thread (with --scan dlb)")
+    ap.add_argument("--retune", action="store_true", help="autotune even when the tuning table has an entry")
+    ap.add_argument("--save-tuning", default=None, help="write the tuning table after autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "sweep", "mixed", "batch", "serving"],
                     help="single: the headline line (default); the others print their own line")
@@ -509,6 +555,22 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     fn = kf.kf_rts_smooth if args.op == "rts" else kf.kf_two_filter_smooth
     mdl = kf.Model(model)
+    tuned = None
+    kf.kf_set_option("threads", args.threads)
+    kf.kf_set_option("lookback_warps", args.lbw)
+    kf.kf_set_option("positions_per_thread", args.k)
+    if args.scan == "auto":
+        # launch configuration (CTA size, look-back warps, tile size) from the
+        # tuning table shipped for GB300, else from the library's autotuner,
+        # chosen before anything is timed
+        kf.kf_tuning_clear()
+        if not args.retune and os.path.exists(TUNING_TABLE):
+            kf.kf_tuning_load(TUNING_TABLE)
+            tuned = kf.kf_tuning_get(args.op, nx, ny, args.precision, T)
+        if tuned is None:
+            tuned = kf.kf_autotune(args.op, model, y, args.precision, reps=5, workspace=ws)
+            if args.save_tuning:
+                kf.kf_tuning_save(args.save_tuning)
 
     def step():
         fn(mdl, y, args.precision, args.scan, ms_out=ms, Ps_out=Ps, loglik=True, workspace=ws)
@@ -631,13 +693,16 @@ def main():
             k["frac"] = (k["tflops"] * 1e12 / alu_peak) if k["bound"] == "alu" else (k["gbs"] * 1e9 / hbm_peak)
     dom = max(kern, key=lambda n: kern[n]["avg_ms"])
     d = kern[dom]
+    cfgname = "threads%d_lbw%d_k%d" % ((tuned["threads"], tuned["lookback_warps"], tuned["steps_per_thread"])
+                                      if tuned else (args.threads, args.lbw, args.k))
+    traffic = recorded_traffic(dom, args.precision, T, cfgname)
     if d["bound"] == "alu":
         roof = {"kernel": dom, "bound": "alu", "achieved": d["tflops"], "peak": alu_peak / 1e12, "unit": "TFLOP/s",
-                "frac": d["frac"], "traffic": None,
+                "frac": d["frac"], "traffic": traffic,
                 "peak_source": peak_src + "; measured FFMA throughput %.1f TFLOP/s" % (fma_peak / 1e12)}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak / 1e9, "unit": "GB/s",
-                "frac": d["frac"], "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                "frac": d["frac"], "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     step_roof = 1.0 / (max(f_flops / alu_peak, fb / hbm_peak) + max(r_flops / alu_peak, rb / hbm_peak))
 
     out = {
@@ -645,7 +710,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp32_fp64solve": "f32+f64solve"}[args.precision],
-        "data": "synthetic (seeded simulation of the model)", "config": workload_config(args, world),
+        "data": "synthetic (seeded simulation of the model)",
+        "config": dict(workload_config(args, world), **({"tuned": tuned} if tuned else {})),
         "roofline": roof,
         "kernels": kern,
         "step_roofline": {"steps_per_s": step_roof, "frac": value / world / step_roof},

@@ -27,8 +27,11 @@
  *     the working precision: double for KF_FP64, float for KF_FP32 and
  *     KF_FP32_FP64SOLVE.  y is [T][ny] (y[k-1] is y_k, k = 1..T); means are
  *     [T][nx]; covariances are full, row-major [T][nx][nx].  Outputs are for
- *     k = 1..T.  Buffers must not overlap and must be aligned to their
- *     element size.
+ *     k = 1..T.  Buffers must not overlap.  Each buffer must be aligned to
+ *     the largest of 16, 8 and 4 bytes that divides the byte size of one of
+ *     its rows (y: ny values; means: nx; covariances: nx * nx), e.g. 16
+ *     bytes for nx = 4 means in float, 8 bytes for ny = 2 in float
+ *     (KF_ERR_ARG otherwise): rows move as 16-, 8- or 4-byte vectors.
  *   - loglik, when not NULL, is a DEVICE pointer to one double that receives
  *     log p(y_{1:T}), accumulated in FP64 in a fixed order.
  *   - workspace: a DEVICE buffer of at least kf_workspace_size(...) bytes,

@@ -356,6 +356,14 @@ static kf_status_t library_workspace(size_t bytes, void **out) {
 
 static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// Rows of `len` values of w bytes move as the widest of 16-, 8- and 4-byte
+// vectors that divides the row: a buffer must be aligned to that width.
+static size_t row_align(int len, size_t w) {
+    const size_t b = size_t(len) * w;
+    return (b % 16 == 0) ? 16 : (b % 8 == 0) ? 8 : 4;
+}
+static bool rows_aligned(const void *p, int len, size_t w) { return !p || aligned(p, row_align(len, w)); }
+
 static kf_status_t check_model(const kf_model_t *md) {
     if (!md) return KF_ERR_ARG;
     if (md->nx != 2 && md->nx != 4 && md->nx != 8) return KF_ERR_ARG;
@@ -437,9 +445,10 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
         q.mf_user = m2;
         q.Pf_user = P2;
     }
-    const void *ptrs[] = {y, m1, P1, m2, P2};
-    for (const void *p : ptrs)
-        if (p && !aligned(p, w)) return KF_ERR_ARG;
+    const int nx = md->nx, ny = md->ny;
+    if (!rows_aligned(y, ny, w) || !rows_aligned(m1, nx, w) || !rows_aligned(P1, nx * nx, w) ||
+        !rows_aligned(m2, nx, w) || !rows_aligned(P2, nx * nx, w))
+        return KF_ERR_ARG;
     if (loglik && !aligned(loglik, 8)) return KF_ERR_ARG;
     if (workspace && !aligned(workspace, 256)) return KF_ERR_ARG;
     HostModel hm;
@@ -558,8 +567,10 @@ static kf_status_t run_batch(kf_op_t op, const kf_model_t *models, int nmodels, 
     }
     for (int i = 0; s == KF_OK && i < nmodels; ++i) s = precompute(&models[i], &hms[i]);
     const size_t w = (prec == KF_FP64) ? 8 : 4;
-    if (s == KF_OK && (!aligned(y, w) || !aligned(m1, w) || (P1 && !aligned(P1, w)) ||
-                       (loglik && !aligned(loglik, 8)) || (workspace && !aligned(workspace, 256))))
+    if (s == KF_OK &&
+        (!rows_aligned(y, models[0].ny, w) || !rows_aligned(m1, models[0].nx, w) ||
+         !rows_aligned(P1, models[0].nx * models[0].nx, w) || (loglik && !aligned(loglik, 8)) ||
+         (workspace && !aligned(workspace, 256))))
         s = KF_ERR_ARG;
     LaunchReq q;
     memset(&q, 0, sizeof(q));
@@ -638,7 +649,8 @@ static kf_status_t rts_noalloc(const kf_model_t *md, int64_t T, const void *y, k
     if (T < 1 || !y || !ms || !Ps) return KF_ERR_ARG;
     if (prec != KF_FP64 && prec != KF_FP32 && prec != KF_FP32_FP64SOLVE) return KF_ERR_ARG;
     const size_t w = (prec == KF_FP64) ? 8 : 4;
-    if (!aligned(y, w) || !aligned(ms, w) || !aligned(Ps, w)) return KF_ERR_ARG;
+    if (!rows_aligned(y, md->ny, w) || !rows_aligned(ms, md->nx, w) || !rows_aligned(Ps, md->nx * md->nx, w))
+        return KF_ERR_ARG;
     if ((loglik && !aligned(loglik, 8)) || (status_out && !aligned(status_out, 4))) return KF_ERR_ARG;
     if (timing_on()) return KF_ERR_ARG;   // kernel timing would create CUDA events
     const size_t need = 256 + ws_bytes_dispatch(md->nx, KF_OP_RTS_I, int(prec), KF_SCAN_DLB_I, T);

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "kf_host.h"
+#include <math.h>
 #include <stdio.h>
 
 #include "scan_levels.cuh"
@@ -51,6 +52,141 @@ void to_params(const HostModel &h, FiltParams<N, R> &p) {
     p.ny = h.m;
 }
 
+// ---------------------------------------------------------------- fold table (host, FP64)
+
+// X = (I + C J)^{-1} (n x n, row-major) by Gauss-Jordan elimination with
+// partial pivoting.
+static inline bool host_inv_I_plus(const double *C, const double *J, int n, double *X) {
+    double a[KF_MAXN * KF_MAXN];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+            double s = (r == c) ? 1.0 : 0.0;
+            for (int k = 0; k < n; ++k) s += C[r * n + k] * J[k * n + c];
+            a[r * n + c] = s;
+            X[r * n + c] = (r == c) ? 1.0 : 0.0;
+        }
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(a[r * n + c]) > fabs(a[p * n + c])) p = r;
+        if (a[p * n + c] == 0.0) return false;
+        if (p != c)
+            for (int k = 0; k < n; ++k) {
+                double t = a[c * n + k];
+                a[c * n + k] = a[p * n + k];
+                a[p * n + k] = t;
+                t = X[c * n + k];
+                X[c * n + k] = X[p * n + k];
+                X[p * n + k] = t;
+            }
+        const double d = 1.0 / a[c * n + c];
+        for (int k = 0; k < n; ++k) {
+            a[c * n + k] *= d;
+            X[c * n + k] *= d;
+        }
+        for (int r = 0; r < n; ++r)
+            if (r != c) {
+                const double f = a[r * n + c];
+                for (int k = 0; k < n; ++k) {
+                    a[r * n + k] -= f * a[c * n + k];
+                    X[r * n + k] -= f * X[c * n + k];
+                }
+            }
+    }
+    return true;
+}
+
+// out (n x q) = a (n x p) b (p x q), row-major
+static inline void host_mm(const double *a, const double *b, int n, int p, int q, double *out) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < q; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < p; ++k) s += a[i * p + k] * b[k * q + j];
+            out[i * q + j] = s;
+        }
+}
+
+// Rows T1 | T4 | T3U for c = 1 .. K-1 and the (A, C, J) of the aggregate of
+// K fresh elements, from the recursion of the (A, C, J) half of Lemma 1
+// (FoldTab):  A_{c+1} = T1_c A_c,  C_{c+1} = T1_c C_c A^T + C,
+// J_{c+1} = A_c^T (I + J C_c)^{-1} J A_c + J_c.  Leaves t.K = 0 when K is
+// outside the table.
+template <int N, int M, typename R>
+static void build_fold_table(const HostModel &h, int K, FoldTab<N, M, R> &t) {
+    using TT = FoldTab<N, M, R>;
+    t.K = 0;
+    if (K < 2 || K - 1 > TT::KT || h.n != N || h.m != M) return;
+    constexpr int NN = N * N;
+    double Ai[NN], Ci[NN], Ji[NN], X[NN], T1[NN], T3[NN], W[NN], V[NN];
+    double AT[NN], Ut[N * M], T4[N * M], T3U[N * M];
+    for (int i = 0; i < NN; ++i) {
+        Ai[i] = h.A[i];
+        Ci[i] = h.C[i];
+        Ji[i] = h.J[i];
+    }
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) AT[r * N + c] = h.A[c * N + r];
+    for (int r = 0; r < N; ++r)
+        for (int i = 0; i < M; ++i) Ut[r * M + i] = h.U[i * N + r];
+    for (int c = 1; c < K; ++c) {
+        if (!host_inv_I_plus(Ci, h.J, N, X)) return;
+        host_mm(h.A, X, N, N, N, T1);   // T1 = A X
+        host_mm(T1, Ci, N, N, N, W);    // W = T1 C_c
+        host_mm(W, h.G, N, N, M, T4);   // T4 = T1 C_c G + K
+        for (int i = 0; i < N * M; ++i) T4[i] += h.K[i];
+        for (int r = 0; r < N; ++r)     // T3 = A_c^T X^T = A_c^T (I + J C_c)^{-1}
+            for (int q = 0; q < N; ++q) {
+                double s = 0.0;
+                for (int k = 0; k < N; ++k) s += Ai[k * N + r] * X[q * N + k];
+                T3[r * N + q] = s;
+            }
+        host_mm(T3, Ut, N, N, M, T3U);  // T3U = T3 U^T
+        R *row = t.t + (c - 1) * TT::E;
+        for (int i = 0; i < NN; ++i) row[i] = R(T1[i]);
+        for (int i = 0; i < N * M; ++i) {
+            row[NN + i] = R(T4[i]);
+            row[NN + N * M + i] = R(T3U[i]);
+        }
+        double An[NN], Cn[NN], Jn[NN];
+        host_mm(T1, Ai, N, N, N, An);
+        host_mm(W, AT, N, N, N, Cn);
+        for (int i = 0; i < NN; ++i) Cn[i] += h.C[i];
+        host_mm(T3, h.J, N, N, N, V);
+        host_mm(V, Ai, N, N, N, Jn);
+        for (int i = 0; i < NN; ++i) Jn[i] += Ji[i];
+        for (int i = 0; i < NN; ++i) {
+            Ai[i] = An[i];
+            Ci[i] = Cn[i];
+            Ji[i] = Jn[i];
+        }
+    }
+    for (int i = 0; i < NN; ++i) t.A[i] = R(Ai[i]);
+    for (int r = 0; r < N; ++r)
+        for (int c = r; c < N; ++c) {
+            t.C[su(N, r, c)] = R(0.5 * (Ci[r * N + c] + Ci[c * N + r]));
+            t.J[su(N, r, c)] = R(0.5 * (Ji[r * N + c] + Ji[c * N + r]));
+        }
+    // the run from a_1: C'_1 = C_1, C'_{c+1} = T1'_c C'_c A^T + C (the filtering covariances)
+    for (int i = 0; i < NN; ++i) Ci[i] = h.C1[i];
+    for (int c = 1; c < K; ++c) {
+        if (!host_inv_I_plus(Ci, h.J, N, X)) return;
+        host_mm(h.A, X, N, N, N, T1);
+        host_mm(T1, Ci, N, N, N, W);
+        host_mm(W, h.G, N, N, M, T4);
+        for (int i = 0; i < N * M; ++i) T4[i] += h.K[i];
+        R *row = t.t1 + (c - 1) * TT::E1;
+        for (int i = 0; i < NN; ++i) row[i] = R(T1[i]);
+        for (int i = 0; i < N * M; ++i) row[NN + i] = R(T4[i]);
+        double Cn[NN];
+        host_mm(W, AT, N, N, N, Cn);
+        for (int i = 0; i < NN; ++i) Ci[i] = Cn[i] + h.C[i];
+    }
+    for (int r = 0; r < N; ++r)
+        for (int c = r; c < N; ++c) t.C1K[su(N, r, c)] = R(0.5 * (Ci[r * N + c] + Ci[c * N + r]));
+    t.K = K;
+}
+static inline void build_fold_table(const HostModel &, int, NoTab &t) { t.K = 0; }
+
 // ---------------------------------------------------------------- tile plan
 
 template <class P, int THREADS, int V, int C>
@@ -98,7 +234,7 @@ static TilePlan plan_tiles(int64_t total, int threads, int window, int resident,
 // Regions, each 256-byte aligned:
 //   ctl_f  : counters[2] + flags[KF_MAX_TILES]   (forward scan)
 //   ctl_r  : counters[2] + flags[KF_MAX_TILES]   (reverse scan)
-//   agg    : KF_MAX_TILES * max element size * sizeof(R)
+//   agg    : KF_MAX_TILES * max element size (padded to 16 bytes) * sizeof(R)
 //   incl   : KF_MAX_TILES * max carry size * sizeof(R)
 //   llpart : KF_MAX_TILES doubles
 //   frec   : filter records [T][FRec::SIZE] (smoothers)
@@ -118,13 +254,14 @@ static inline int64_t next_pow2(int64_t t) {
 template <int N, typename R>
 WsLayout ws_layout(int op, int scan, int64_t T) {
     constexpr int ES = FElem<N, R>::SIZE;  // >= RElem size
+    constexpr int ESP = ((ES * int(sizeof(R)) + 15) / 16) * 16 / int(sizeof(R));
     constexpr int CS = FwdCarry<N, R>::SIZE;
     WsLayout L;
     size_t o = 0;
     const size_t ctl = al256(sizeof(int) * (2 + KF_MAX_TILES));
     L.ctl_f = o; o += ctl;
     L.ctl_r = o; o += ctl;
-    L.agg = o; o += al256(size_t(KF_MAX_TILES) * ES * sizeof(R));
+    L.agg = o; o += al256(size_t(KF_MAX_TILES) * ESP * sizeof(R));
     L.incl = o; o += al256(size_t(KF_MAX_TILES) * CS * sizeof(R));
     L.llpart = o; o += al256(size_t(KF_MAX_TILES) * sizeof(double));
     L.frec = L.lv_a = L.lv_b = 0;
@@ -144,17 +281,44 @@ WsLayout ws_layout(int op, int scan, int64_t T) {
 
 // Time steps per lane staged at once: as many as keep one CTA's staging
 // buffers within 96 KB (at most 8).
+// Shared-memory budget of a CTA's staging buffers.
+#ifndef KF_STAGE_BYTES
+#define KF_STAGE_BYTES (96 * 1024)
+#endif
 template <class P, int THREADS>
 constexpr int stage_chunk() {
     constexpr int bpp = 32 * (2 * P::IN_REC + P::O1 + P::O2 + P::O3) * int(sizeof(typename P::R));
-    constexpr int c = (96 * 1024) / ((THREADS / 32) * bpp);
+    constexpr int c = (KF_STAGE_BYTES) / ((THREADS / 32) * bpp);
     return c < 1 ? 1 : (c > 8 ? 8 : c);
 }
 
 // Per-warp shared-memory layout of the staging buffers actually used.
-template <class P, int C>
+// A buffer is left out (records read or written in place) when staging
+// every array would take more than 160 KB of shared memory per CTA: outputs
+// first, largest first, then the input.
+template <class P, int C, int THREADS>
 static void stage_layout(const typename P::Args &args, DlbCtl &ctl) {
     using R = typename P::R;
+    constexpr int NW = THREADS / 32, LIMIT = 160 * 1024;
+    const int in_bytes = P::IN_REC ? WarpStage<C, (P::IN_REC ? P::IN_REC : 1), R>::BYTES : 0;
+    const int sizes[3] = {WarpStage<C, (P::O1 ? P::O1 : 1), R>::BYTES, WarpStage<C, (P::O2 ? P::O2 : 1), R>::BYTES,
+                          WarpStage<C, (P::O3 ? P::O3 : 1), R>::BYTES};
+    const int recs[3] = {P::O1, P::O2, P::O3};
+    bool use_in = P::IN_REC != 0, use_out[3];
+    for (int i = 0; i < 3; ++i) use_out[i] = recs[i] && P::out_arr(args, i);
+    auto need = [&]() {
+        int b = use_in ? 2 * ((in_bytes + 15) & ~15) : 0;
+        for (int i = 0; i < 3; ++i) b += use_out[i] ? (sizes[i] + 15) & ~15 : 0;
+        return b * NW + P::tab_bytes();
+    };
+    while (need() > LIMIT) {
+        int big = -1;
+        for (int i = 0; i < 3; ++i)
+            if (use_out[i] && (big < 0 || sizes[i] > sizes[big])) big = i;
+        if (big >= 0) use_out[big] = false;
+        else if (use_in) use_in = false;
+        else break;
+    }
     int o = 0;
     auto take = [&](int bytes) {
         const int at = o;
@@ -162,14 +326,11 @@ static void stage_layout(const typename P::Args &args, DlbCtl &ctl) {
         return at;
     };
     ctl.sm_in0 = ctl.sm_in1 = -1;
-    if (P::IN_REC) {
-        ctl.sm_in0 = take(WarpStage<C, (P::IN_REC ? P::IN_REC : 1), R>::BYTES);
-        ctl.sm_in1 = take(WarpStage<C, (P::IN_REC ? P::IN_REC : 1), R>::BYTES);
+    if (use_in) {
+        ctl.sm_in0 = take(in_bytes);
+        ctl.sm_in1 = take(in_bytes);
     }
-    const int sizes[3] = {WarpStage<C, (P::O1 ? P::O1 : 1), R>::BYTES, WarpStage<C, (P::O2 ? P::O2 : 1), R>::BYTES,
-                          WarpStage<C, (P::O3 ? P::O3 : 1), R>::BYTES};
-    const int recs[3] = {P::O1, P::O2, P::O3};
-    for (int i = 0; i < 3; ++i) ctl.sm_out[i] = (recs[i] && P::out_arr(args, i)) ? take(sizes[i]) : -1;
+    for (int i = 0; i < 3; ++i) ctl.sm_out[i] = use_out[i] ? take(sizes[i]) : -1;
     ctl.sm_warp = o;
 }
 
@@ -182,8 +343,14 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
     if (debug_on()) fprintf(stderr, "[kfscan] run_dlb\n");
     const int64_t total = P::total(args);
     DlbCtl ctl;
-    stage_layout<P, C>(args, ctl);
-    const int smem = ctl.sm_warp * (THREADS / 32);
+    stage_layout<P, C, THREADS>(args, ctl);
+    ctl.sm_tab = -1;
+    int smem = ctl.sm_warp * (THREADS / 32);
+    typename P::Args a2 = args;
+    if constexpr (P::TABLE) {
+        ctl.sm_tab = smem;
+        smem += P::tab_bytes();
+    }
     static int attr_smem = 0;   // dynamic shared memory already allowed for this instantiation
     if (smem > attr_smem) {
         cudaError_t e = cudaFuncSetAttribute(dlb_scan_kernel<P, THREADS, V, C>,
@@ -193,6 +360,10 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
     }
     const TilePlan tp =
         plan_tiles(total, THREADS, THREADS * V, max_resident_tiles<P, THREADS, V, C>(dev, smem), q.k_override);
+    if constexpr (P::TABLE) {
+        build_fold_table(*q.hm, tp.K, a2.tab);
+        if (a2.tab.K == 0) ctl.sm_tab = -1;
+    }
     ctl.counters = reinterpret_cast<int *>(ws + ctl_off);
     ctl.flags = ctl.counters + 2;
     ctl.agg = ws + L.agg;
@@ -216,7 +387,7 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
     if (e != cudaSuccess) return e;
     cudaEvent_t t0 = nullptr;
     if (timing_on()) timing_record(P::KIND, q.stream, &t0);
-    dlb_scan_kernel<P, THREADS, V, C><<<tp.ntiles, THREADS, smem, q.stream>>>(args, ctl);
+    dlb_scan_kernel<P, THREADS, V, C><<<tp.ntiles, THREADS, smem, q.stream>>>(a2, ctl);
     e = cudaGetLastError();
     count_launches(P::KIND, 1);
     if (t0) timing_commit(P::KIND, q.stream, t0);
@@ -302,6 +473,32 @@ static cudaError_t run_scan(const typename P::Args &args, char *ws, size_t ctl_o
 
 // ---------------------------------------------------------------- one operation
 
+// The forward pass with the general or the low-rank operator forms, through
+// the requested scan algorithm (DLB_ONLY: always the decoupled look-back scan).
+template <int N, typename R, int MODE, class Src, int THREADS, int V, bool DLB_ONLY>
+static cudaError_t filter_pass(const typename FilterFwd<N, R, MODE, Src>::Args &fa, bool lowrank, char *ws,
+                               const WsLayout &L, const LaunchReq &q, double *ll) {
+    constexpr int LRM = N / 2;
+    if (lowrank) {
+        using PF = FilterFwd<N, R, MODE, Src, LRM>;
+        typename PF::Args fl;
+        fl.src = fa.src;
+        fl.buf = fa.buf;
+        fl.want_ll = fa.want_ll;
+        fl.tab.K = 0;
+        if constexpr (DLB_ONLY) return run_dlb<PF, THREADS, V>(fl, ws, L.ctl_f, L, q, ll);
+        else return run_scan<PF, THREADS, V>(fl, ws, L.ctl_f, L, q, ll);
+    }
+    using PG = FilterFwd<N, R, MODE, Src, 0>;
+    typename PG::Args fg;
+    fg.src = fa.src;
+    fg.buf = fa.buf;
+    fg.want_ll = fa.want_ll;
+    fg.tab.K = 0;
+    if constexpr (DLB_ONLY) return run_dlb<PG, THREADS, V>(fg, ws, L.ctl_f, L, q, ll);
+    else return run_scan<PG, THREADS, V>(fg, ws, L.ctl_f, L, q, ll);
+}
+
 template <int N, typename R, int MODE, int THREADS>
 static cudaError_t launch_typed(const LaunchReq &q) {
     using Src = OneSeq<N, R>;
@@ -320,18 +517,13 @@ static cudaError_t launch_typed(const LaunchReq &q) {
 
     typename FilterFwd<N, R, MODE, Src>::Args fa;
     to_params<N, R>(*q.hm, fa.src.prm);
+    fa.tab.K = 0;
     fa.src.T = q.T;
     fa.buf = buf;
     fa.want_ll = q.loglik != nullptr;
-    cudaError_t e;
-    constexpr int LRM = N / 2;   // low-rank filter path when ny = nx / 2
-    if (q.hm->m == LRM && q.scan == KF_SCAN_DLB_I && !q.no_lowrank) {
-        typename FilterFwd<N, R, MODE, Src, LRM>::Args fl;
-        memcpy(&fl, &fa, sizeof(fl));
-        e = run_scan<FilterFwd<N, R, MODE, Src, LRM>, THREADS, V>(fl, ws, L.ctl_f, L, q, q.loglik);
-    } else {
-        e = run_scan<FilterFwd<N, R, MODE, Src>, THREADS, V>(fa, ws, L.ctl_f, L, q, q.loglik);
-    }
+    // low-rank filter path when ny = nx / 2
+    const bool lowrank = q.hm->m == N / 2 && q.scan == KF_SCAN_DLB_I && !q.no_lowrank;
+    cudaError_t e = filter_pass<N, R, MODE, Src, THREADS, V, false>(fa, lowrank, ws, L, q, q.loglik);
     if (e != cudaSuccess || q.op == KF_OP_FILTER_I) return e;
     if (q.op == KF_OP_RTS_I) {
         typename RtsRev<N, R, Src>::Args ra;
@@ -420,16 +612,11 @@ static cudaError_t launch_batch_typed(const LaunchReq &q, const BatchReq &b) {
     qq.ll_step = q.loglik ? reinterpret_cast<double *>(ws + B.ll_step) : nullptr;
     typename FilterFwd<N, R, MODE, Src>::Args fa;
     fa.src = src;
+    fa.tab.K = 0;
     fa.buf = buf;
     fa.want_ll = q.loglik != nullptr;
-    constexpr int LRM = N / 2;
-    if (b.all_ny_half && !q.no_lowrank) {
-        typename FilterFwd<N, R, MODE, Src, LRM>::Args fl;
-        memcpy(&fl, &fa, sizeof(fl));
-        e = run_dlb<FilterFwd<N, R, MODE, Src, LRM>, THREADS, V>(fl, ws, L.ctl_f, L, qq, nullptr);
-    } else {
-        e = run_dlb<FilterFwd<N, R, MODE, Src>, THREADS, V>(fa, ws, L.ctl_f, L, qq, nullptr);
-    }
+    const bool lowrank = b.all_ny_half && !q.no_lowrank;
+    e = filter_pass<N, R, MODE, Src, THREADS, V, true>(fa, lowrank, ws, L, qq, nullptr);
     if (e != cudaSuccess) return e;
     if (q.loglik) {
         const int threads = 256, blocks = int((int64_t(b.nseq) * 32 + threads - 1) / threads);

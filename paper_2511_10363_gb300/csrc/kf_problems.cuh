@@ -22,6 +22,8 @@
 // (eta, J) half off from everything after it.
 #pragma once
 
+#include <type_traits>
+
 #include "kf_math.cuh"
 
 namespace kfs {
@@ -29,12 +31,14 @@ namespace kfs {
 // Where the model constants of a position come from.
 template <int N, typename R>
 struct OneSeq {
+    static constexpr bool ONE = true;
     FiltParams<N, R> prm;
     int64_t T;
 };
 
 template <int N, typename R>
 struct ManySeq {
+    static constexpr bool ONE = false;
     const FiltParams<N, R> *prm;   // [nmodels]
     const int *model_of;           // [nseg] model of each sequence
     const int64_t *offsets;        // [nseg + 1], offsets[0] = 0, non-decreasing
@@ -190,6 +194,44 @@ KF_D void op_tf_merge(const R *x, const R *Pk, const RevCarry<N, R> &c, R *ms, R
 // pointers, which point either into a warp's shared-memory staging buffer or
 // straight into device memory.
 
+// ---------------------------------------------------------------- fold table
+//
+// For a time-invariant model every fresh element a_k (k >= 2) has the same
+// (A, C, J), with b_k = K y_k and eta_k = G y_k.  When a thread folds c fresh
+// elements from the left, the (A, C, J) half of its running aggregate is
+// therefore a function of c alone, and Lemma 1 with the fresh element on the
+// right reduces to two affine updates of (b, eta):
+//   b   <- T1_c b + T4_c y_k,                  T1_c  = A (I + C_c J)^{-1},
+//                                              T4_c  = T1_c C_c G + K,
+//   eta <- eta + T3U_c (L^{-1} y_k - U b),     T3U_c = A_c^T (I + J C_c)^{-1} U^T,
+// using G = U^T L^{-1} and J = U^T U (U = L^{-1} H F, S = L L^T).  (A_c, C_c)
+// is the aggregate of c fresh elements.  The host computes the rows for
+// c = 1 .. K-1 and the (A, C, J) of the K-element aggregate in FP64 for the
+// launch's K (positions per thread); the kernel copies the rows into shared
+// memory and every thread whose K positions are all fresh elements of one
+// sequence folds with them.
+//
+// The run that starts at a_1 (A_1 = 0) has its own rows: its aggregate keeps
+// A = 0 and (eta, J) = (eta_1, J_1) = (G y_1, J) (Lemma 1 with A_i = 0), and
+// its C_c is the filtering covariance P_{c|c}, so only
+// T1'_c = A (I + P_{c|c} J)^{-1} and T4'_c = T1'_c P_{c|c} G + K are needed.
+template <int N, int M, typename R>
+struct FoldTab {
+    static constexpr int S = N * (N + 1) / 2;
+    static constexpr int E = N * N + 2 * N * M;                       // row: T1 | T4 | T3U
+    static constexpr int E1 = N * N + N * M;                          // first-run row: T1' | T4'
+    static constexpr int KT0 = 8192 / (E * int(sizeof(R)));
+    static constexpr int KT = KT0 < 64 ? KT0 : 64;                    // rows (<= 8 KB)
+    int K;                                                            // 0: no table
+    R A[N * N], C[S], J[S];                                           // aggregate of K fresh elements
+    R C1K[S];                                                         // P_{K|K}: C of the first run
+    alignas(16) R t[KT * E];
+    alignas(16) R t1[KT * E1];
+};
+struct NoTab {
+    int K;
+};
+
 // LR > 0: every fresh element's J is U^T U of rank LR = ny, and the thread
 // fold and the carry pass use the low-rank forms (kf_math.cuh).
 template <int N, typename Rt, int MODE, class Src, int LR = 0>
@@ -202,13 +244,145 @@ struct FilterFwd {
     static constexpr int S = N * (N + 1) / 2;
     // the low-rank path knows ny = LR at compile time and stages y as its input record
     static constexpr int IN_REC = LR, O1 = FRec<N, R>::SIZE, O2 = N, O3 = N * N;
+    // table-driven thread fold: low-rank path, one sequence, nx <= 4
+    static constexpr bool TABLE = LR > 0 && N <= 4 && Src::ONE;
+    using Tab = typename std::conditional<TABLE, FoldTab<N, (LR > 0 ? LR : 1), R>, NoTab>::type;
     struct Args {
         Src src;
         KfBufs<R> buf;
         int want_ll;
+        Tab tab;
+    };
+    struct TabFold {
+        R b[N], eta[N];
+        int c;
+        bool first;   // the run starts at a_1
     };
     static KF_HD int64_t total(const Args &a) { return seq_total(a.src); }
     static KF_HD const R *in_arr(const Args &a) { return LR > 0 ? a.buf.y : nullptr; }
+    // rows of the fold table in bytes (0: none)
+    static constexpr int tab_bytes() {
+        if constexpr (TABLE) return Tab::KT * Tab::E * int(sizeof(R)); else return 0;
+    }
+    // Copy the table rows into shared memory (all threads of the CTA).
+    static KF_D void tab_load(const Args &a, R *dst) {
+        if constexpr (TABLE) {
+            const int n4 = (a.tab.K > 1 ? (a.tab.K - 1) * Tab::E : 0) * int(sizeof(R)) / 16;
+            const float4 *src = reinterpret_cast<const float4 *>(a.tab.t);
+            float4 *d = reinterpret_cast<float4 *>(dst);
+            for (int i = threadIdx.x; i < n4; i += blockDim.x) d[i] = src[i];
+        }
+    }
+    // Does this thread's run [start, end) fold with the table?  It must hold
+    // K positions (the sequence starts at position 0).
+    static KF_D bool tab_fast(const Args &a, int64_t start, int64_t end, int K) {
+        if constexpr (TABLE) return a.tab.K == K && K >= 2 && end - start == K;
+        else return false;
+    }
+    static KF_D void tab_step(const Args &a, int64_t p, const R *in, const R *tab, TabFold &f) {
+        if constexpr (TABLE) {
+            const FiltParams<N, R> &P = a.src.prm;
+            R y[LR];
+            load_rec<LR>(y, y_of(a, p, in, LR));
+            if (f.c == 0) {
+                f.first = (p == 0);
+                if (f.first) {   // a_1: b_1 = c1 + K1 y_1, eta_1 = G y_1
+                    Elem e;
+                    build_filter_elem<N, R>(P, 1, y, e);
+#pragma unroll
+                    for (int i = 0; i < N; ++i) {
+                        f.b[i] = e.v[Elem::ob + i];
+                        f.eta[i] = e.v[Elem::oe + i];
+                    }
+                } else {
+                    fresh_b_eta<N, LR, R>(P, y, f.b, f.eta);
+                }
+            } else if (f.first) {
+                constexpr int E1 = Tab::E1;
+                const R *row = a.tab.t1 + (f.c - 1) * E1;   // read in place (one thread)
+                const R *T1 = row, *T4 = row + N * N;
+                R nb[N];
+#pragma unroll
+                for (int r = 0; r < N; ++r) {
+                    R s = 0;
+#pragma unroll
+                    for (int j = 0; j < LR; ++j) s += T4[r * LR + j] * y[j];
+#pragma unroll
+                    for (int k = 0; k < N; ++k) s += T1[r * N + k] * f.b[k];
+                    nb[r] = s;
+                }
+#pragma unroll
+                for (int r = 0; r < N; ++r) f.b[r] = nb[r];
+            } else {
+                constexpr int E = Tab::E;
+                R row[E];
+                load_rec<E>(row, tab + (f.c - 1) * E);
+                const R *T1 = row, *T4 = row + N * N, *T3U = row + N * N + N * LR;
+                R v[LR];   // whitened innovation L^{-1} y - U b
+#pragma unroll
+                for (int i = 0; i < LR; ++i) {
+                    R s = 0;
+#pragma unroll
+                    for (int k = 0; k <= i; ++k) s += P.Linv[i * MAXNY + k] * y[k];
+#pragma unroll
+                    for (int k = 0; k < N; ++k) s -= P.U[i * N + k] * f.b[k];
+                    v[i] = s;
+                }
+                R nb[N];
+#pragma unroll
+                for (int r = 0; r < N; ++r) {
+                    R s = 0;
+#pragma unroll
+                    for (int j = 0; j < LR; ++j) s += T4[r * LR + j] * y[j];
+#pragma unroll
+                    for (int k = 0; k < N; ++k) s += T1[r * N + k] * f.b[k];
+                    nb[r] = s;
+                }
+#pragma unroll
+                for (int r = 0; r < N; ++r) {
+                    R s = f.eta[r];
+#pragma unroll
+                    for (int i = 0; i < LR; ++i) s += T3U[r * LR + i] * v[i];
+                    f.eta[r] = s;
+                }
+#pragma unroll
+                for (int r = 0; r < N; ++r) f.b[r] = nb[r];
+            }
+            ++f.c;
+        }
+    }
+    static KF_D void tab_finish(const Args &a, const TabFold &f, Elem &agg) {
+        if constexpr (TABLE) {
+            if (f.first) {   // A = 0, C = P_{K|K}, (eta, J) = (eta_1, J_1)
+                const FiltParams<N, R> &P = a.src.prm;
+#pragma unroll
+                for (int i = 0; i < N * N; ++i) agg.v[Elem::oA + i] = R(0);
+#pragma unroll
+                for (int i = 0; i < S; ++i) {
+                    agg.v[Elem::oC + i] = a.tab.C1K[i];
+                    agg.v[Elem::oJ + i] = P.J[i];
+                }
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    agg.v[Elem::ob + i] = f.b[i];
+                    agg.v[Elem::oe + i] = f.eta[i];
+                }
+                return;
+            }
+#pragma unroll
+            for (int i = 0; i < N * N; ++i) agg.v[Elem::oA + i] = a.tab.A[i];
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                agg.v[Elem::oC + i] = a.tab.C[i];
+                agg.v[Elem::oJ + i] = a.tab.J[i];
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                agg.v[Elem::ob + i] = f.b[i];
+                agg.v[Elem::oe + i] = f.eta[i];
+            }
+        }
+    }
     static KF_HD R *out_arr(const Args &a, int i) { return i == 0 ? a.buf.frec : i == 1 ? a.buf.mf_user : a.buf.Pf_user; }
     static KF_D SegCursor cursor(const Args &a, int64_t p) { return seg_find(a.src, p); }
     static KF_D void build(const Args &a, int64_t p, SegCursor &cur, const R *in, Elem &e) {
@@ -235,7 +409,8 @@ struct FilterFwd {
 #pragma unroll
         for (int i = 0; i < S; ++i) c.v[Carry::oC + i] = e.v[Elem::oC + i];
     }
-    static KF_D void emit(const Args &, const Carry &c, const R *, R *o1, R *o2, R *o3) {
+    // outputs of the position p (global index p) whose prefix carry is c
+    static KF_D void emit(const Args &, int64_t, SegCursor &, const Carry &c, const R *, R *o1, R *o2, R *o3) {
         const R *b = c.v + Carry::ob, *C = c.v + Carry::oC;
         if (o1) {
             R rec[O1];
@@ -290,7 +465,7 @@ struct FilterFwd {
     // w = eta_k - J b = F^T H^T S^{-1} v, v^T S_k^{-1} v = v^T S^{-1} v - w^T D w,
     // D = (I + C J)^{-1} C (matrix determinant lemma and Woodbury identity).
     // c <- c (x) a_p, outputs of p, log-likelihood term of p
-    static KF_D double step_at(const Args &a, int64_t p, SegCursor &cur, Carry &c, const R *in, R *o1, R *o2, R *o3) {
+    static KF_D R step_at(const Args &a, int64_t p, SegCursor &cur, Carry &c, const R *in, R *o1, R *o2, R *o3) {
         if constexpr (LR > 0) {
             seg_move(a.src, cur, p);
             const FiltParams<N, R> &P = seg_params(a.src, cur);
@@ -298,7 +473,7 @@ struct FilterFwd {
                 R yv[LR], b[N], eta[N];
                 load_rec<LR>(yv, y_of(a, p, in, LR));
                 fresh_b_eta<N, LR, R>(P, yv, b, eta);
-                double ll = 0.0;
+                R ll = 0;
                 if (a.want_ll) {
                     R yt[LR];
 #pragma unroll
@@ -317,7 +492,7 @@ struct FilterFwd {
                         apply_fwd_lr_parts<N, LR, R, MODE, true>(c, P.A, b, P.C, eta, P.U, yt, &q, &ld);
                     }
                     // the per-step term in the working precision; FP64 only accumulates
-                    ll = double(R(-0.5) * (q + ld + P.llc_r));
+                    ll = R(-0.5) * (q + ld + P.llc_r);
                 } else {
                     if constexpr (N >= 8) {
                         Elem e;
@@ -327,19 +502,19 @@ struct FilterFwd {
                         apply_fwd_lr_parts<N, LR, R, MODE, false>(c, P.A, b, P.C, eta, P.U, nullptr, nullptr, nullptr);
                     }
                 }
-                emit(a, c, in, o1, o2, o3);
+                emit(a, p, cur, c, in, o1, o2, o3);
                 return ll;
             }
         }
         Elem e;
         build(a, p, cur, in, e);
-        return step(a, p, cur, c, e, in, o1, o2, o3);
+        return R(step(a, p, cur, c, e, in, o1, o2, o3));
     }
     static KF_D double step(const Args &a, int64_t p, SegCursor &cur, Carry &c, const Elem &e, const R *in, R *o1,
                             R *o2, R *o3) {
         if (!a.want_ll) {
             apply_fresh(a, cur, c, e);
-            emit(a, c, in, o1, o2, o3);
+            emit(a, p, cur, c, in, o1, o2, o3);
             return 0.0;
         }
         const FiltParams<N, R> &P = seg_params(a.src, cur);
@@ -391,7 +566,7 @@ struct FilterFwd {
             op_apply_fwd<N, R, MODE, true>(c, e, &ld, &wDw);
             ll = -0.5 * (double(q) - double(wDw) + P.llc + ld);
         }
-        emit(a, c, in, o1, o2, o3);
+        emit(a, p, cur, c, in, o1, o2, o3);
         return ll;
     }
 };
@@ -412,6 +587,13 @@ struct TfRev {
         KfBufs<R> buf;
         int want_ll;
     };
+    static constexpr bool TABLE = false;
+    struct TabFold {};
+    static constexpr int tab_bytes() { return 0; }
+    static KF_D void tab_load(const Args &, R *) {}
+    static KF_D bool tab_fast(const Args &, int64_t, int64_t, int) { return false; }
+    static KF_D void tab_step(const Args &, int64_t, const R *, const R *, TabFold &) {}
+    static KF_D void tab_finish(const Args &, const TabFold &, Elem &) {}
     static KF_HD int64_t total(const Args &a) { return seq_total(a.src); }
     static KF_HD const R *in_arr(const Args &a) { return a.buf.frec; }
     static KF_HD R *out_arr(const Args &a, int i) { return i == 0 ? a.buf.ms : i == 1 ? a.buf.Ps : nullptr; }
@@ -438,7 +620,7 @@ struct TfRev {
         for (int i = 0; i < S; ++i) c.v[Carry::oJ + i] = e.v[Elem::oJ + i];
     }
     // merge with the filter record (Eqs. mean_tf_combination / cov_tf_combination)
-    static KF_D void emit(const Args &, const Carry &c, const R *in, R *o1, R *o2, R *) {
+    static KF_D void emit(const Args &, int64_t, SegCursor &, const Carry &c, const R *in, R *o1, R *o2, R *) {
         R rec[IN_REC], ms[N], Ps[S], full[N * N];
         load_rec<IN_REC>(rec, in);
         op_tf_merge<N, R, MODE>(rec, rec + N, c, ms, Ps);
@@ -452,15 +634,15 @@ struct TfRev {
         combine(agg, e, t);
         agg = t;
     }
-    static KF_D double step_at(const Args &a, int64_t p, SegCursor &cur, Carry &c, const R *in, R *o1, R *o2, R *o3) {
+    static KF_D R step_at(const Args &a, int64_t p, SegCursor &cur, Carry &c, const R *in, R *o1, R *o2, R *o3) {
         Elem e;
         build(a, p, cur, in, e);
         return step(a, p, cur, c, e, in, o1, o2, o3);
     }
-    static KF_D double step(const Args &a, int64_t, SegCursor &, Carry &c, const Elem &e, const R *in, R *o1, R *o2,
-                            R *o3) {
+    static KF_D double step(const Args &a, int64_t p, SegCursor &cur, Carry &c, const Elem &e, const R *in, R *o1,
+                            R *o2, R *o3) {
         apply(c, e);
-        emit(a, c, in, o1, o2, o3);
+        emit(a, p, cur, c, in, o1, o2, o3);
         return 0.0;
     }
 };
@@ -481,6 +663,13 @@ struct RtsRev {
         KfBufs<R> buf;
         int want_ll;
     };
+    static constexpr bool TABLE = false;
+    struct TabFold {};
+    static constexpr int tab_bytes() { return 0; }
+    static KF_D void tab_load(const Args &, R *) {}
+    static KF_D bool tab_fast(const Args &, int64_t, int64_t, int) { return false; }
+    static KF_D void tab_step(const Args &, int64_t, const R *, const R *, TabFold &) {}
+    static KF_D void tab_finish(const Args &, const TabFold &, Elem &) {}
     static KF_HD int64_t total(const Args &a) { return seq_total(a.src); }
     static KF_HD const R *in_arr(const Args &a) { return a.buf.frec; }
     static KF_HD R *out_arr(const Args &a, int i) { return i == 0 ? a.buf.ms : i == 1 ? a.buf.Ps : nullptr; }
@@ -488,10 +677,9 @@ struct RtsRev {
     static KF_D void build(const Args &a, int64_t p, SegCursor &cur, const R *in, Elem &e) {
         const int64_t g = seq_total(a.src) - 1 - p;
         seg_move(a.src, cur, g);
-        const FiltParams<N, R> &P = seg_params(a.src, cur);
         R rec[IN_REC];
         load_rec<IN_REC>(rec, in);
-        op_build_rts<N, R>(P, g == cur.e - 1, rec, rec + N, e);
+        op_build_rts<N, R>(seg_params(a.src, cur), g == cur.e - 1, rec, rec + N, e);
     }
     static KF_D void fold_at(const Args &a, int64_t p, SegCursor &cur, const R *in, Elem &agg) {
         Elem e, t;
@@ -499,7 +687,7 @@ struct RtsRev {
         combine(agg, e, t);
         agg = t;
     }
-    static KF_D double step_at(const Args &a, int64_t p, SegCursor &cur, Carry &c, const R *in, R *o1, R *o2, R *o3) {
+    static KF_D R step_at(const Args &a, int64_t p, SegCursor &cur, Carry &c, const R *in, R *o1, R *o2, R *o3) {
         Elem e;
         build(a, p, cur, in, e);
         return step(a, p, cur, c, e, in, o1, o2, o3);
@@ -513,16 +701,16 @@ struct RtsRev {
 #pragma unroll
         for (int i = 0; i < S; ++i) c.v[Carry::oL + i] = e.v[Elem::oL + i];
     }
-    static KF_D void emit(const Args &, const Carry &c, const R *, R *o1, R *o2, R *) {
+    static KF_D void emit(const Args &, int64_t, SegCursor &, const Carry &c, const R *, R *o1, R *o2, R *) {
         R full[N * N];
         store_rec<N>(o1, c.v + Carry::og);
         store_full<N>(full, c.v + Carry::oL);
         store_rec<N * N>(o2, full);
     }
-    static KF_D double step(const Args &a, int64_t, SegCursor &, Carry &c, const Elem &e, const R *in, R *o1, R *o2,
-                            R *o3) {
+    static KF_D double step(const Args &a, int64_t p, SegCursor &cur, Carry &c, const Elem &e, const R *in, R *o1,
+                            R *o2, R *o3) {
         apply(c, e);
-        emit(a, c, in, o1, o2, o3);
+        emit(a, p, cur, c, in, o1, o2, o3);
         return 0.0;
     }
 };

@@ -4,7 +4,8 @@
 // One CTA scans one tile of THREADS * K consecutive scan positions:
 //   1. take a tile ticket (atomic counter), so every tile that a CTA waits
 //      for was claimed by a CTA that is already running;
-//   2. each thread builds its K elements and folds them (full operator);
+//   2. each thread builds its K elements and folds them (full operator, or
+//      the problem's fold table when it has one and the run qualifies);
 //   3. a warp Kogge-Stone scan (shuffles) and a scan of the warp aggregates
 //      give every thread its exclusive prefix inside the tile and the tile
 //      aggregate, which is published (flag 1);
@@ -34,7 +35,7 @@ namespace kfs {
 struct DlbCtl {
     int *counters;         // [0] tile ticket, [1] finished-tile count
     int *flags;            // [ntiles] 0 empty, 1 aggregate, 2 inclusive
-    void *agg;             // [ntiles][Elem::SIZE]
+    void *agg;             // [ntiles][Elem::SIZE padded to 16 bytes]
     void *incl;            // [ntiles][Carry::SIZE]
     double *ll_part;       // [ntiles] per-tile log-likelihood partial sums
     double *ll_out;        // final log-likelihood (nullable)
@@ -45,8 +46,10 @@ struct DlbCtl {
     int K;                 // positions per thread
     int inject_skip_tile;  // test hook: this tile never publishes (-1: none)
     // per-warp dynamic shared memory: byte offsets of the staging buffers
-    // (input double buffer, three outputs; -1 = absent) and the warp stride
+    // (input double buffer, three outputs; -1 = not staged: the records are
+    // read or written in place) and the warp stride
     int sm_in0, sm_in1, sm_out[3], sm_warp;
+    int sm_tab;            // byte offset of the fold-table rows (-1: none)
     int lbw;               // warps that take part in the look-back (1 .. THREADS/32)
     uint64_t *trace;       // optional [ntiles][8] %globaltimer stamps at phase boundaries
     int trace_cap;         // tiles the trace buffer holds
@@ -107,6 +110,44 @@ KF_D void load_cg(X &x, const R *src) {
     for (int i = 0; i < X::SIZE; ++i) x.v[i] = __ldcg(src + i);
 }
 
+// Elements published for the look-back sit at a stride padded to 16 bytes
+// and move as 16-byte vectors (L2 only: other SMs wrote them).
+template <class X, typename R>
+constexpr int padded_size() {
+    return ((X::SIZE * int(sizeof(R)) + 15) / 16) * 16 / int(sizeof(R));
+}
+template <class X, typename R>
+KF_D void load_cg_vec(X &x, const R *src) {
+    constexpr int P = padded_size<X, R>(), W = 16 / int(sizeof(R));
+    R t[P];
+#pragma unroll
+    for (int i = 0; i < P / W; ++i) {
+        if constexpr (sizeof(R) == 4) {
+            const float4 v = __ldcg(reinterpret_cast<const float4 *>(src) + i);
+            t[4 * i] = v.x; t[4 * i + 1] = v.y; t[4 * i + 2] = v.z; t[4 * i + 3] = v.w;
+        } else {
+            const double2 v = __ldcg(reinterpret_cast<const double2 *>(src) + i);
+            t[2 * i] = v.x; t[2 * i + 1] = v.y;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < X::SIZE; ++i) x.v[i] = t[i];
+}
+template <class X, typename R>
+KF_D void store_vec(R *dst, const X &x) {
+    constexpr int P = padded_size<X, R>(), W = 16 / int(sizeof(R));
+    R t[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) t[i] = i < X::SIZE ? x.v[i] : R(0);
+#pragma unroll
+    for (int i = 0; i < P / W; ++i) {
+        if constexpr (sizeof(R) == 4)
+            reinterpret_cast<float4 *>(dst)[i] = make_float4(t[4 * i], t[4 * i + 1], t[4 * i + 2], t[4 * i + 3]);
+        else
+            reinterpret_cast<double2 *>(dst)[i] = make_double2(t[2 * i], t[2 * i + 1]);
+    }
+}
+
 // Global record index of scan position p, and the first record of the
 // C-record segment that holds positions [p0, p0 + C) (record order is the
 // global order, so a reverse scan walks its segment backwards).
@@ -117,8 +158,25 @@ KF_D int64_t seg_first(int64_t total, int64_t p0) { return P::REV ? total - p0 -
 template <class P, int C>
 KF_D int seg_slot(int c) { return P::REV ? C - 1 - c : c; }
 
+// Resident CTAs per SM that the register allocation of a 128-thread scan
+// CTA must allow, per scan kind (filter, RTS, two-filter).
+#ifndef KF_DLB_MINB_FILTER
+#define KF_DLB_MINB_FILTER 1
+#endif
+#ifndef KF_DLB_MINB_RTS
+#define KF_DLB_MINB_RTS 1
+#endif
+#ifndef KF_DLB_MINB_TF
+#define KF_DLB_MINB_TF 1
+#endif
+template <class P, int THREADS>
+constexpr int dlb_min_blocks() {
+    if (THREADS != 128) return 1;
+    return P::KIND == 0 ? KF_DLB_MINB_FILTER : P::KIND == 1 ? KF_DLB_MINB_RTS : KF_DLB_MINB_TF;
+}
+
 template <class P, int THREADS, int V, int C>
-__global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant__ typename P::Args args,
+__global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_scan_kernel(const __grid_constant__ typename P::Args args,
                                                            const DlbCtl ctl) {
     using R = typename P::R;
     using Elem = typename P::Elem;
@@ -131,6 +189,11 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
     __shared__ int s_tile, s_qstar, s_abort, s_last;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    R *const tab = (P::TABLE && ctl.sm_tab >= 0) ? reinterpret_cast<R *>(dsm + ctl.sm_tab) : nullptr;
+    if constexpr (P::TABLE) {
+        if (tab) P::tab_load(args, tab);
+    }
     if (tid == 0) {
         s_tile = atomicAdd(ctl.counters, 1);
         s_qstar = -1;
@@ -145,10 +208,10 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
     const int64_t start = (int64_t(tile) * THREADS + tid) * ctl.K;
     const int64_t end = start + ctl.K < total ? start + ctl.K : total;
 
-    extern __shared__ __align__(16) unsigned char dsm[];
     unsigned char *wsm = dsm + warp * ctl.sm_warp;
-    unsigned char *const in0 = P::IN_REC ? wsm + ctl.sm_in0 : nullptr;
-    unsigned char *const in1 = P::IN_REC ? wsm + ctl.sm_in1 : nullptr;
+    // staged input (null: the records are read in place)
+    unsigned char *const in0 = (P::IN_REC && ctl.sm_in0 >= 0) ? wsm + ctl.sm_in0 : nullptr;
+    unsigned char *const in1 = (P::IN_REC && ctl.sm_in1 >= 0) ? wsm + ctl.sm_in1 : nullptr;
     const int nchunks = (ctl.K + C - 1) / C;
     const R *in_arr = P::in_arr(args);
 
@@ -156,13 +219,16 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
     Elem agg;
     {
         bool have = false;
+        const bool fast = tab && P::tab_fast(args, start, end, ctl.K);
+        typename P::TabFold tf;
+        if constexpr (P::TABLE) tf.c = 0;
         SegCursor cur = P::cursor(args, start < total ? start : total - 1);
-        if constexpr (P::IN_REC > 0) {
+        if (P::IN_REC > 0 && in0) {
             stage_load<C, P::IN_REC>(in_arr, seg_first<P, C>(total, start), total, in0, lane);
             cp_async_commit();
         }
         for (int ch = 0; ch < nchunks; ++ch) {
-            if constexpr (P::IN_REC > 0) {
+            if (P::IN_REC > 0 && in0) {
                 if (ch + 1 < nchunks) {
                     stage_load<C, P::IN_REC>(in_arr, seg_first<P, C>(total, start + (ch + 1) * C), total,
                                              ((ch + 1) & 1) ? in1 : in0, lane);
@@ -177,7 +243,15 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
             for (int c = 0; c < C; ++c) {
                 const int64_t p = start + ch * C + c;
                 if (p >= end) break;
-                const R *in = P::IN_REC ? stage_rec<C, P::IN_REC, R>((ch & 1) ? in1 : in0, lane, seg_slot<P, C>(c)) : nullptr;
+                const R *in = !P::IN_REC ? nullptr
+                              : in0 ? stage_rec<C, P::IN_REC, R>((ch & 1) ? in1 : in0, lane, seg_slot<P, C>(c))
+                                    : in_arr + gidx<P>(total, p) * P::IN_REC;
+                if constexpr (P::TABLE) {
+                    if (fast) {
+                        P::tab_step(args, p, in, tab, tf);
+                        continue;
+                    }
+                }
                 if (!have) {
                     P::build(args, p, cur, in, agg);
                     have = true;
@@ -186,6 +260,12 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
                 }
             }
             __syncwarp();
+        }
+        if constexpr (P::TABLE) {
+            if (fast) {
+                P::tab_finish(args, tf, agg);
+                have = true;
+            }
         }
         if (!have) set_identity(agg);
     }
@@ -243,14 +323,14 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
 #pragma unroll
     for (int i = 0; i < ES; ++i) tagg.v[i] = s_red[0][i];
 
-    // publish the tile aggregate (tile 0 publishes its inclusive prefix directly)
-    if (tile > 0) {
-        R *dst = static_cast<R *>(ctl.agg) + int64_t(tile) * ES;
-        for (int i = tid; i < ES; i += THREADS) dst[i] = tagg.v[i];
-        __threadfence();
+    // publish the tile aggregate (tile 0 publishes its inclusive prefix
+    // directly); the release store orders the data stores before the flag
+    constexpr int ESP = padded_size<Elem, R>();
+    if (tile > 0 && tid == 0) {
+        store_vec(static_cast<R *>(ctl.agg) + int64_t(tile) * ESP, tagg);
+        st_release(ctl.flags + tile, 1);
     }
     __syncthreads();
-    if (tile > 0 && tid == 0) st_release(ctl.flags + tile, 1);
     if (trace) trace[2] = global_ns();
 
     // ---- 4. look-back
@@ -288,7 +368,7 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
                 const int q = tile - 1 - (tid * vv + v);
                 if (q > qstar) {
                     Elem a;
-                    load_cg(a, static_cast<const R *>(ctl.agg) + int64_t(q) * ES);
+                    load_cg_vec(a, static_cast<const R *>(ctl.agg) + int64_t(q) * ESP);
                     if (!have) {
                         x = a;
                         have = true;
@@ -381,12 +461,12 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
         for (int i = 0; i < 3; ++i) obuf[i] = (ctl.sm_out[i] >= 0 && oarr[i]) ? wsm + ctl.sm_out[i] : nullptr;
         // this lane's own global record range, for the stores
         const int64_t lo = P::REV ? total - end : start, hi = P::REV ? total - start : end;
-        if constexpr (P::IN_REC > 0) {
+        if (P::IN_REC > 0 && in0) {
             stage_load<C, P::IN_REC>(in_arr, seg_first<P, C>(total, start), total, in0, lane);
             cp_async_commit();
         }
         for (int ch = 0; ch < nchunks; ++ch) {
-            if constexpr (P::IN_REC > 0) {
+            if (P::IN_REC > 0 && in0) {
                 if (ch + 1 < nchunks) {
                     stage_load<C, P::IN_REC>(in_arr, seg_first<P, C>(total, start + (ch + 1) * C), total,
                                              ((ch + 1) & 1) ? in1 : in0, lane);
@@ -403,13 +483,19 @@ __global__ void __launch_bounds__(THREADS) dlb_scan_kernel(const __grid_constant
                 const int64_t p = start + ch * C + cc;
                 if (p >= end) break;
                 const int slot = seg_slot<P, C>(cc);
-                const R *in = P::IN_REC ? stage_rec<C, P::IN_REC, R>((ch & 1) ? in1 : in0, lane, slot) : nullptr;
-                R *o1 = obuf[0] ? stage_rec<C, (P::O1 ? P::O1 : 1), R>(obuf[0], lane, slot) : nullptr;
-                R *o2 = obuf[1] ? stage_rec<C, (P::O2 ? P::O2 : 1), R>(obuf[1], lane, slot) : nullptr;
-                R *o3 = obuf[2] ? stage_rec<C, (P::O3 ? P::O3 : 1), R>(obuf[2], lane, slot) : nullptr;
-                const double l = P::step_at(args, p, cur, c, in, o1, o2, o3);
-                llc += R(l);
-                if (ctl.ll_step) ctl.ll_step[gidx<P>(total, p)] = l;
+                const int64_t g = gidx<P>(total, p);
+                const R *in = !P::IN_REC ? nullptr
+                              : in0 ? stage_rec<C, P::IN_REC, R>((ch & 1) ? in1 : in0, lane, slot)
+                                    : in_arr + g * P::IN_REC;
+                R *o1 = obuf[0] ? stage_rec<C, (P::O1 ? P::O1 : 1), R>(obuf[0], lane, slot)
+                                : (P::O1 && oarr[0]) ? oarr[0] + g * P::O1 : nullptr;
+                R *o2 = obuf[1] ? stage_rec<C, (P::O2 ? P::O2 : 1), R>(obuf[1], lane, slot)
+                                : (P::O2 && oarr[1]) ? oarr[1] + g * P::O2 : nullptr;
+                R *o3 = obuf[2] ? stage_rec<C, (P::O3 ? P::O3 : 1), R>(obuf[2], lane, slot)
+                                : (P::O3 && oarr[2]) ? oarr[2] + g * P::O3 : nullptr;
+                const R l = P::step_at(args, p, cur, c, in, o1, o2, o3);
+                llc += l;
+                if (ctl.ll_step) ctl.ll_step[g] = double(l);
             }
             ll += double(llc);   // FP64 accumulation, once per chunk of at most C steps
             __syncwarp();

@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(THREADS) lv_extract(const __grid_constant__ ty
             Carry c;
             load_soa(s, a, Tpad, p);
             P::carry_of(s, c);
-            P::emit(args, c, in, o1, o2, o3);
+            P::emit(args, p, cur, c, in, o1, o2, o3);
         }
     }
     if (!ll_out) return;

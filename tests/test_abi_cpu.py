@@ -66,6 +66,9 @@ def test_argument_errors(lib):
     assert call_filter(good, prec=7) == 1                    # bad enum
     assert call_filter(good, scan=9) == 1
     assert call_filter(good, y=ctypes.c_void_p((1 << 20) + 2)) == 1   # misaligned
+    # rows move as vectors: ny = 2 floats need 8-byte, nx = 4 float means 16-byte alignment
+    assert call_filter(good, y=ctypes.c_void_p((1 << 20) + 4)) == 1
+    assert call_filter(good, m=ctypes.c_void_p((1 << 20) + 8)) == 1
     bad = dict(good)
     bad["F"] = np.eye(3)
     bad["H"] = np.zeros((2, 3))

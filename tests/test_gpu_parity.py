@@ -131,3 +131,25 @@ def test_filter_solve_forms(general, precision, nx):
             compare(op, model, y, precision, "dlb")
     finally:
         kf.kf_set_option("general_solve", 0)
+
+
+@pytest.mark.parametrize("K", [2, 3, 16, 33, 34, 65, 66, 200])
+@pytest.mark.parametrize("model_kind", ["cv", "random4", "random2"])
+def test_fold_table(K, model_kind):
+    """With ny = nx / 2 and one sequence, the thread fold of the filter scan
+    reads the (A, C, J) half of its aggregate from a table built per launch
+    for K positions per thread (up to 65 rows in FP32, 33 in FP64; beyond
+    that the per-step solve is used).  Forced K across the table limits, a
+    ragged last thread and many tiles."""
+    import paper_2511_10363_gb300 as kf
+    model = {"cv": W.cv_model(), "random4": W.random_stable_model(4, 2, seed=K),
+             "random2": W.random_model(2, 1, seed=K)}[model_kind]
+    T = K * 128 * 5 + 77
+    y = W.simulate(model, T, seed=500 + K)
+    kf.kf_set_option("positions_per_thread", K)
+    try:
+        for precision in PRECS:
+            compare("filter", model, y, precision, "dlb")
+        compare("rts", model, y, "fp32", "dlb")
+    finally:
+        kf.kf_set_option("positions_per_thread", 0)
