@@ -169,9 +169,25 @@ struct FiltParams {
 
 // ---------------------------------------------------------------- small solves
 
-// Correctly rounded reciprocal (the CUDA intrinsic for FP32).
-KF_D float recip(float x) { return __frcp_rn(x); }
+// Reciprocal, square root and natural log of the small solves.  FP32: the
+// hardware approximations (PTX rcp.approx / sqrt.approx, MUFU log2; relative
+// error about 2^-23, a few ulp for the log), far below the FP32 tolerance of
+// the outputs and cheaper than the correctly rounded sequences.  FP64:
+// correctly rounded.
+KF_D float recip(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 KF_D double recip(double x) { return __drcp_rn(x); }
+KF_D float ksqrt(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+KF_D double ksqrt(double x) { return sqrt(x); }
+KF_D float klog(float x) { return __logf(x); }
+KF_D double klog(double x) { return log(x); }
 
 // X = (I + C J)^{-1} for packed symmetric C, J, by Gauss-Jordan elimination
 // with partial pivoting in precision T.  Returns sum log|pivot| = log det(I + C J)
@@ -215,7 +231,7 @@ KF_D void inv_I_plus_CJ_T(const RC *C, const RJ *J, T X[N * N], T &logdet) {
             }
         }
         const T piv = a[c * N + c];
-        if (LD) logdet += log(fabs(piv));
+        if (LD) logdet += klog(fabs(piv));
         const T d = recip(piv);
 #pragma unroll
         for (int j = c + 1; j < N; ++j) a[c * N + j] *= d;
@@ -602,14 +618,14 @@ template <int M, typename T>
 KF_D void spd_inverse(const T *Pp, T *W, T &logdet) {
     if constexpr (M == 1) {
         W[0] = recip(Pp[0]);
-        logdet = log(Pp[0]);
+        logdet = klog(Pp[0]);
     } else if constexpr (M == 2) {
         const T det = Pp[0] * Pp[2] - Pp[1] * Pp[1];
         const T r = recip(det);
         W[0] = Pp[2] * r;
         W[1] = -Pp[1] * r;
         W[2] = Pp[0] * r;
-        logdet = log(det);
+        logdet = klog(det);
     } else {
         T L[M * (M + 1) / 2], dinv[M];
         T ld = 0;
@@ -621,10 +637,10 @@ KF_D void spd_inverse(const T *Pp, T *W, T &logdet) {
 #pragma unroll
                 for (int k = 0; k < j; ++k) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
                 if (i == j) {
-                    const T d = sqrt(s);
+                    const T d = ksqrt(s);
                     L[i * (i + 1) / 2 + i] = d;
                     dinv[i] = recip(d);
-                    ld += log(s);
+                    ld += klog(s);
                 } else {
                     L[i * (i + 1) / 2 + j] = s * dinv[j];
                 }
@@ -1172,7 +1188,7 @@ KF_D void build_rts_elem(const FiltParams<N, R> &P, bool last, const R *x, const
 #pragma unroll
             for (int k = 0; k < j; ++k) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
             if (i == j) {
-                const R d = sqrt(s);
+                const R d = ksqrt(s);
                 L[i * (i + 1) / 2 + i] = d;
                 dinv[i] = recip(d);
             } else {

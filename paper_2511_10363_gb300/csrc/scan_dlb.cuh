@@ -206,6 +206,8 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
     if (trace) trace[0] = global_ns();
     const int64_t total = P::total(args);
     const int64_t start = (int64_t(tile) * THREADS + tid) * ctl.K;
+    const int64_t start0 = (int64_t(tile) * THREADS + warp * 32) * ctl.K;   // lane 0's run
+    const int64_t dK = P::REV ? -int64_t(ctl.K) : int64_t(ctl.K);
     const int64_t end = start + ctl.K < total ? start + ctl.K : total;
 
     unsigned char *wsm = dsm + warp * ctl.sm_warp;
@@ -224,13 +226,13 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
         if constexpr (P::TABLE) tf.c = 0;
         SegCursor cur = P::cursor(args, start < total ? start : total - 1);
         if (P::IN_REC > 0 && in0) {
-            stage_load<C, P::IN_REC>(in_arr, seg_first<P, C>(total, start), total, in0, lane);
+            stage_load<C, (P::IN_REC > 0 ? P::IN_REC : 1)>(in_arr, seg_first<P, C>(total, start0), dK, total, in0, lane);
             cp_async_commit();
         }
         for (int ch = 0; ch < nchunks; ++ch) {
             if (P::IN_REC > 0 && in0) {
                 if (ch + 1 < nchunks) {
-                    stage_load<C, P::IN_REC>(in_arr, seg_first<P, C>(total, start + (ch + 1) * C), total,
+                    stage_load<C, (P::IN_REC > 0 ? P::IN_REC : 1)>(in_arr, seg_first<P, C>(total, start0 + (ch + 1) * C), dK, total,
                                              ((ch + 1) & 1) ? in1 : in0, lane);
                     cp_async_commit();
                     cp_async_wait<1>();
@@ -459,16 +461,14 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
         void *obuf[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) obuf[i] = (ctl.sm_out[i] >= 0 && oarr[i]) ? wsm + ctl.sm_out[i] : nullptr;
-        // this lane's own global record range, for the stores
-        const int64_t lo = P::REV ? total - end : start, hi = P::REV ? total - start : end;
         if (P::IN_REC > 0 && in0) {
-            stage_load<C, P::IN_REC>(in_arr, seg_first<P, C>(total, start), total, in0, lane);
+            stage_load<C, (P::IN_REC > 0 ? P::IN_REC : 1)>(in_arr, seg_first<P, C>(total, start0), dK, total, in0, lane);
             cp_async_commit();
         }
         for (int ch = 0; ch < nchunks; ++ch) {
             if (P::IN_REC > 0 && in0) {
                 if (ch + 1 < nchunks) {
-                    stage_load<C, P::IN_REC>(in_arr, seg_first<P, C>(total, start + (ch + 1) * C), total,
+                    stage_load<C, (P::IN_REC > 0 ? P::IN_REC : 1)>(in_arr, seg_first<P, C>(total, start0 + (ch + 1) * C), dK, total,
                                              ((ch + 1) & 1) ? in1 : in0, lane);
                     cp_async_commit();
                     cp_async_wait<1>();
@@ -499,10 +499,13 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
             }
             ll += double(llc);   // FP64 accumulation, once per chunk of at most C steps
             __syncwarp();
-            const int64_t gs = seg_first<P, C>(total, start + ch * C);
-            if constexpr (P::O1 > 0) if (obuf[0]) stage_store<C, P::O1>(oarr[0], gs, lo, hi, obuf[0], lane);
-            if constexpr (P::O2 > 0) if (obuf[1]) stage_store<C, P::O2>(oarr[1], gs, lo, hi, obuf[1], lane);
-            if constexpr (P::O3 > 0) if (obuf[2]) stage_store<C, P::O3>(oarr[2], gs, lo, hi, obuf[2], lane);
+            const int64_t gs0 = seg_first<P, C>(total, start0 + ch * C);
+            if constexpr (P::O1 > 0)
+                if (obuf[0]) stage_store<C, P::O1, P::REV>(oarr[0], gs0, start0, ctl.K, total, obuf[0], lane);
+            if constexpr (P::O2 > 0)
+                if (obuf[1]) stage_store<C, P::O2, P::REV>(oarr[1], gs0, start0, ctl.K, total, obuf[1], lane);
+            if constexpr (P::O3 > 0)
+                if (obuf[2]) stage_store<C, P::O3, P::REV>(oarr[2], gs0, start0, ctl.K, total, obuf[2], lane);
             __syncwarp();
         }
     }

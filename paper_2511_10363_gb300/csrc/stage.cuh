@@ -61,11 +61,15 @@ struct UnitT<8> { using T = float2; };
 template <>
 struct UnitT<4> { using T = float; };
 
-// Issue the asynchronous load of records [gs, gs + C) of every lane's run,
-// gs = this lane's first record index; records outside [0, total) are
-// skipped.  `buf` is this warp's buffer.
+// The runs of a warp: lane r's run starts at scan position start0 + r K, and
+// its segment of the current chunk begins at global record gs0 + r dK
+// (dK = K for a forward scan, -K for a reverse one).  Computing these per
+// unit replaces a shuffle of the owner lane's values.
+
+// Issue the asynchronous load of the C records of every lane's run segment;
+// records outside [0, total) are skipped.  `buf` is this warp's buffer.
 template <int C, int REC, typename R>
-KF_D void stage_load(const R *gbase, int64_t gs, int64_t total, void *buf, int lane) {
+KF_D void stage_load(const R *gbase, int64_t gs0, int64_t dK, int64_t total, void *buf, int lane) {
     using W = WarpStage<C, REC, R>;
     using UT = typename UnitT<W::U>::T;
     const UT *g = reinterpret_cast<const UT *>(gbase);
@@ -73,15 +77,16 @@ KF_D void stage_load(const R *gbase, int64_t gs, int64_t total, void *buf, int l
 #pragma unroll 4
     for (int idx = lane; idx < 32 * W::SEGU; idx += 32) {
         const int run = idx / W::SEGU, o = idx - run * W::SEGU;
-        const int64_t rec = __shfl_sync(0xffffffffu, gs, run) + o / W::RU;
+        const int64_t rec = gs0 + run * dK + o / W::RU;
         if (rec >= 0 && rec < total) cp_async_unit<W::U>(s + run * W::STRIDE + o, g + rec * W::RU + o % W::RU);
     }
 }
 
-// Store the staged records [gs, gs + C) of every lane's run whose index lies
-// in [lo, hi) of that lane (its own positions), coalesced.
-template <int C, int REC, typename R>
-KF_D void stage_store(R *gbase, int64_t gs, int64_t lo, int64_t hi, const void *buf, int lane) {
+// Store the staged records of every lane's run segment that lie in that
+// lane's own global record range (the records of positions
+// [start, min(start + K, total)) of its run), coalesced.
+template <int C, int REC, bool REV, typename R>
+KF_D void stage_store(R *gbase, int64_t gs0, int64_t start0, int64_t K, int64_t total, const void *buf, int lane) {
     using W = WarpStage<C, REC, R>;
     using UT = typename UnitT<W::U>::T;
     UT *g = reinterpret_cast<UT *>(gbase);
@@ -89,10 +94,17 @@ KF_D void stage_store(R *gbase, int64_t gs, int64_t lo, int64_t hi, const void *
 #pragma unroll 4
     for (int idx = lane; idx < 32 * W::SEGU; idx += 32) {
         const int run = idx / W::SEGU, o = idx - run * W::SEGU;
-        const int64_t base = __shfl_sync(0xffffffffu, gs, run);
-        const int64_t l = __shfl_sync(0xffffffffu, lo, run), h = __shfl_sync(0xffffffffu, hi, run);
-        const int64_t rec = base + o / W::RU;
-        if (rec >= l && rec < h) g[rec * W::RU + o % W::RU] = s[run * W::STRIDE + o];
+        const int64_t st = start0 + run * K;
+        int64_t lo, hi;
+        if constexpr (REV) {
+            hi = total - st;
+            lo = hi - K > 0 ? hi - K : 0;
+        } else {
+            lo = st;
+            hi = st + K < total ? st + K : total;
+        }
+        const int64_t rec = gs0 + (REV ? -run * K : run * K) + o / W::RU;
+        if (rec >= lo && rec < hi) g[rec * W::RU + o % W::RU] = s[run * W::STRIDE + o];
     }
 }
 
