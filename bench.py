@@ -109,6 +109,28 @@ def step_bytes(n, m, w):
     return filt, rts
 
 
+# ------------------------------------------------------------------ ranks
+
+def rank_sequence_seed(rank):
+    """Weak scaling: every rank smooths its own sequence, simulated from its own seed."""
+    return 1 + rank
+
+
+def max_over_ranks(dist, x, device):
+    """The largest x over all ranks (the slowest rank sets the job's time);
+    x itself when there is no process group."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, T, max_ms):
+    """Whole-job throughput: the time steps of all ranks over the slowest rank's time."""
+    return world * steps * T / (max_ms * 1e-3)
+
+
 # ------------------------------------------------------------------ DRAM traffic
 
 def kernel_source_hash():
@@ -545,7 +567,7 @@ def main():
     nx, ny, T = 4, 2, args.T
     dt = kf.dtype_of(args.precision)
     w = 8 if args.precision == "fp64" else 4
-    y_host = torch.tensor(W.simulate(model, T, seed=1 + rank), dtype=dt).pin_memory()
+    y_host = torch.tensor(W.simulate(model, T, seed=rank_sequence_seed(rank)), dtype=dt).pin_memory()
     y = y_host.to("cuda")
     ms = torch.empty((T, nx), dtype=dt, device="cuda")
     Ps = torch.empty((T, nx, nx), dtype=dt, device="cuda")
@@ -623,11 +645,8 @@ def main():
         n_l, _ = kf.timing_read(kd)
         launches += n_l
 
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * args.steps * T / (max_ms * 1e-3)
+    max_ms = max_over_ranks(dist, total_ms, "cuda")
+    value = job_rate(world, args.steps, T, max_ms)
 
     if args.profile:
         if rank == 0:
@@ -654,10 +673,7 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * ek * T / (float(te.item()) * 1e-3)
+    e2e_value = job_rate(world, ek, T, max_over_ranks(dist, e2e_ms, "cuda"))
 
     if rank != 0:
         if dist:
