@@ -279,27 +279,50 @@ WsLayout ws_layout(int op, int scan, int64_t T) {
 
 // ---------------------------------------------------------------- one scan
 
-// Time steps per lane staged at once: as many as keep one CTA's staging
-// buffers within 96 KB (at most 8).
-// Shared-memory budget of a CTA's staging buffers.
+// Time steps per lane staged at once: the most (at most KF_STAGE_CMAX) that keep one
+// CTA's staging buffers within its share of shared memory -- 96 KB for
+// 128-thread CTAs (two per SM), 180 KB for 256-thread CTAs (one per SM).
+// The forward pass writes either its records (smoothers) or the filtering
+// means and covariances (plain filter), so it is sized for the larger of the
+// two sets; a call that asks for both may have to write some outputs in
+// place (stage_layout).
 #ifndef KF_STAGE_BYTES
-#define KF_STAGE_BYTES (96 * 1024)
+#define KF_STAGE_BYTES(threads) ((threads) >= 256 ? 180 * 1024 : 96 * 1024)
 #endif
-template <class P, int THREADS>
+template <class P, int C, int REC>
+constexpr int stage_buf_bytes() {
+    if constexpr (REC == 0) return 0;
+    else return WarpStage<C, REC, typename P::R>::BYTES;
+}
+template <class P, int C>
+constexpr int stage_bytes_warp() {   // one warp
+    constexpr int in = 2 * stage_buf_bytes<P, C, P::IN_REC>();
+    constexpr int o1 = stage_buf_bytes<P, C, P::O1>(), o2 = stage_buf_bytes<P, C, P::O2>(),
+                  o3 = stage_buf_bytes<P, C, P::O3>();
+    if constexpr (P::KIND == 0) return in + (o1 > o2 + o3 ? o1 : o2 + o3);
+    else return in + o1 + o2 + o3;
+}
+// Upper bound of C per pass, measured on GB300 (T = 2^20 and 2^22, FP32,
+// nx = 4): the forward pass is fastest with up to 4 staged steps, the
+// reverse passes with at most 2 (3 or more cost the RTS pass 10-20%).
+#ifndef KF_STAGE_CMAX
+#define KF_STAGE_CMAX(kind) ((kind) == 0 ? 4 : 2)
+#endif
+template <class P, int THREADS, int C = KF_STAGE_CMAX(P::KIND)>
 constexpr int stage_chunk() {
-    constexpr int bpp = 32 * (2 * P::IN_REC + P::O1 + P::O2 + P::O3) * int(sizeof(typename P::R));
-    constexpr int c = (KF_STAGE_BYTES) / ((THREADS / 32) * bpp);
-    return c < 1 ? 1 : (c > 8 ? 8 : c);
+    if constexpr (C <= 1) return 1;
+    else if constexpr (stage_bytes_warp<P, C>() * (THREADS / 32) <= KF_STAGE_BYTES(THREADS)) return C;
+    else return stage_chunk<P, THREADS, C - 1>();
 }
 
 // Per-warp shared-memory layout of the staging buffers actually used.
 // A buffer is left out (records read or written in place) when staging
-// every array would take more than 160 KB of shared memory per CTA: outputs
+// every array would take more than 180 KB of shared memory per CTA: outputs
 // first, largest first, then the input.
 template <class P, int C, int THREADS>
 static void stage_layout(const typename P::Args &args, DlbCtl &ctl) {
     using R = typename P::R;
-    constexpr int NW = THREADS / 32, LIMIT = 160 * 1024;
+    constexpr int NW = THREADS / 32, LIMIT = 180 * 1024;
     const int in_bytes = P::IN_REC ? WarpStage<C, (P::IN_REC ? P::IN_REC : 1), R>::BYTES : 0;
     const int sizes[3] = {WarpStage<C, (P::O1 ? P::O1 : 1), R>::BYTES, WarpStage<C, (P::O2 ? P::O2 : 1), R>::BYTES,
                           WarpStage<C, (P::O3 ? P::O3 : 1), R>::BYTES};
