@@ -390,6 +390,11 @@ def workload_batch(args):
         run = lambda: kf.kf_batch_smooth("rts", model, offs, yt, prec, m_out=m, P_out=P, loglik=True, workspace=ws)
         tb = _timed(run)
         assert kf.kf_sync_status() == 0
+        # the same batched call captured in a CUDA graph and replayed
+        g = kf.BatchGraph("rts", model, offs, yt, prec, loglik=True)
+        tg = _timed(g.launch)
+        assert kf.kf_sync_status() == 0
+        g.close()
         # one launch per sequence, back to back; completion time of each
         mdl = kf.Model(model)
         wsp = torch.empty(kf.kf_workspace_size("rts", 4, 2, int(lengths.max()), prec, "dlb"), dtype=torch.uint8,
@@ -407,6 +412,8 @@ def workload_batch(args):
         done = np.array([evs[0].elapsed_time(e) for e in evs[1:]])
         res[prec] = {"batched": {"ms": tb, "steps_per_s": total / (tb * 1e-3), "latency_p50_ms": tb,
                                  "latency_p99_ms": tb, "launches_per_pass": 1},
+                     "batched_cuda_graph": {"ms": tg, "steps_per_s": total / (tg * 1e-3), "latency_p50_ms": tg,
+                                            "latency_p99_ms": tg},
                      "one_launch_per_sequence": {"ms": float(done[-1]), "steps_per_s": total / (done[-1] * 1e-3),
                                                  "latency_p50_ms": float(np.percentile(done, 50)),
                                                  "latency_p99_ms": float(np.percentile(done, 99))}}

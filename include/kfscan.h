@@ -154,6 +154,26 @@ kf_status_t kf_batch_smooth(kf_op_t op, const kf_model_t *models, int nmodels, c
                             int nseq, const int64_t *offsets, const void *y, kf_precision_t prec, void *m_out,
                             void *P_out, double *loglik, void *workspace, void *stream);
 
+/* The batched call captured in a CUDA graph.  kf_batch_graph_create runs
+ * kf_batch_smooth once with these arguments (writing the outputs) on a
+ * private stream, with a workspace that the graph owns (cudaMalloc'd here),
+ * then captures the same call -- the look-back counter resets and the
+ * kernels of both passes and of the log-likelihood reduction, with the
+ * model constants, offsets and model indices left resident in the graph's
+ * workspace -- and instantiates it.  kf_batch_graph_launch replays the
+ * call on `stream` on the current contents of y (same device buffers, same
+ * shapes, models and offsets; new measurements may be written into y
+ * between launches).  Launches of one graph must not overlap on the GPU
+ * (they share its workspace): launch them on one stream.  Launch
+ * configuration options (KF_OPT_*) are taken at creation; kf_timing_enable
+ * must be off.  kf_batch_graph_destroy frees the graph and its workspace. */
+typedef struct kf_batch_graph kf_batch_graph_t;
+kf_status_t kf_batch_graph_create(kf_op_t op, const kf_model_t *models, int nmodels, const int32_t *model_of_seq,
+                                  int nseq, const int64_t *offsets, const void *y, kf_precision_t prec, void *m_out,
+                                  void *P_out, double *loglik, kf_batch_graph_t **graph);
+kf_status_t kf_batch_graph_launch(kf_batch_graph_t *graph, void *stream);
+kf_status_t kf_batch_graph_destroy(kf_batch_graph_t *graph);
+
 /* Continuous-batching server.  A scheduler thread owns one device arena of
  * budget_bytes (allocated once, here) and max_inflight CUDA streams on the
  * device current at creation.  Submitted jobs wait in a FIFO queue; whenever

@@ -87,6 +87,11 @@ def lib():
         L.kf_rts_smooth_noalloc.argtypes = [MP, i64, vp, i, vp, vp, vp, vp, vp]
         L.kf_batch_smooth.argtypes = [i, MP, i, vp, i, vp, vp, i, vp, vp, vp, vp, vp]
         L.kf_batch_smooth.restype = ctypes.c_int
+        L.kf_batch_graph_create.argtypes = [i, MP, i, vp, i, vp, vp, i, vp, vp, vp, ctypes.POINTER(vp)]
+        L.kf_batch_graph_launch.argtypes = [vp, vp]
+        L.kf_batch_graph_destroy.argtypes = [vp]
+        for f in ("kf_batch_graph_create", "kf_batch_graph_launch", "kf_batch_graph_destroy"):
+            getattr(L, f).restype = ctypes.c_int
         L.kf_batch_workspace_size.argtypes = [i, i, i, i64, i, i, i, i]
         L.kf_batch_workspace_size.restype = ctypes.c_size_t
         L.kf_server_create.argtypes = [ctypes.c_size_t, i, i64, ctypes.POINTER(vp)]
@@ -336,6 +341,52 @@ def kf_batch_smooth(op, models, offsets, y, precision="fp32", model_of=None, m_o
                                _ptr(m_out), _ptr(P_out), _ptr(ll), _ptr(workspace), _stream(stream))
     _check(rc, "kf_batch_smooth")
     return m_out, P_out, ll
+
+
+class BatchGraph:
+    """kf_batch_graph_* of kfscan.h: one batched call captured in a CUDA graph
+    on fixed device buffers.  Construction runs the call once (filling
+    m_out, P_out, ll); launch() replays it on the current contents of y."""
+
+    def __init__(self, op, models, offsets, y, precision="fp32", model_of=None, loglik=False):
+        import torch
+        ms = [_as_model(m) for m in models] if isinstance(models, (list, tuple)) else [_as_model(models)]
+        self._keep = ms
+        arr = (_Model * len(ms))(*[m.c for m in ms])
+        offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        nseq = len(offs) - 1
+        mof = None if model_of is None else np.ascontiguousarray(np.asarray(model_of, dtype=np.int32))
+        dt = dtype_of(precision)
+        total = int(offs[-1])
+        if not (isinstance(y, torch.Tensor) and y.is_cuda and y.dtype == dt and y.is_contiguous()
+                and y.shape == (total, ms[0].ny)):
+            raise ValueError("y must be a contiguous CUDA tensor [total, ny] of dtype %s" % dt)
+        nx = ms[0].nx
+        self.y = y
+        self.m = torch.empty((total, nx), dtype=dt, device=y.device)
+        self.P = torch.empty((total, nx, nx), dtype=dt, device=y.device)
+        self.ll = torch.empty(nseq, dtype=torch.float64, device=y.device) if loglik else None
+        self.h = ctypes.c_void_p()
+        _check(lib().kf_batch_graph_create(OPS[op], arr, len(ms),
+                                           None if mof is None else mof.ctypes.data_as(ctypes.c_void_p), nseq,
+                                           offs.ctypes.data_as(ctypes.c_void_p), _ptr(y), PRECISIONS[precision],
+                                           _ptr(self.m), _ptr(self.P), _ptr(self.ll), ctypes.byref(self.h)),
+               "kf_batch_graph_create")
+
+    def launch(self, stream=None):
+        _check(lib().kf_batch_graph_launch(self.h, _stream(stream)), "kf_batch_graph_launch")
+        return self.m, self.P, self.ll
+
+    def close(self):
+        if self.h:
+            lib().kf_batch_graph_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -7,6 +7,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <new>
 
 #include <atomic>
 #include <map>
@@ -542,7 +543,7 @@ static kf_status_t fma_peak(double *out) {
 
 static kf_status_t run_batch(kf_op_t op, const kf_model_t *models, int nmodels, const int32_t *model_of, int nseq,
                              const int64_t *offsets, const void *y, kf_precision_t prec, void *m1, void *P1,
-                             double *loglik, void *workspace, void *stream) {
+                             double *loglik, void *workspace, void *stream, int params_resident = 0) {
     if (op < KF_OP_FILTER || op > KF_OP_TWO_FILTER) return KF_ERR_ARG;
     if (!models || nmodels < 1 || nseq < 1 || !offsets || !y || !m1) return KF_ERR_ARG;
     if (op != KF_OP_FILTER && !P1) return KF_ERR_ARG;
@@ -611,6 +612,7 @@ static kf_status_t run_batch(kf_op_t op, const kf_model_t *models, int nmodels, 
         b.model_of = mof;
         b.hms = hms;
         b.all_ny_half = (ny == nx / 2);
+        b.params_resident = params_resident;
         s = from_cuda(launch_batch_dispatch(q, b));
     }
     free(mof);
@@ -753,6 +755,84 @@ kf_status_t kf_batch_smooth(kf_op_t op, const kf_model_t *models, int nmodels, c
                             double *loglik, void *workspace, void *stream) {
     return run_batch(op, models, nmodels, model_of_seq, nseq, offsets, y, prec, m_out, P_out, loglik, workspace,
                      stream);
+}
+
+// ---------------------------------------------------------------- batch graphs
+
+struct kf_batch_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    void *ws;
+    int64_t kernels[KF_KERNEL_KINDS];   // kernel launches one replay makes, per kind
+};
+
+kf_status_t kf_batch_graph_create(kf_op_t op, const kf_model_t *models, int nmodels, const int32_t *model_of_seq,
+                                  int nseq, const int64_t *offsets, const void *y, kf_precision_t prec, void *m_out,
+                                  void *P_out, double *loglik, kf_batch_graph_t **graph) {
+    if (!graph) return KF_ERR_ARG;
+    *graph = nullptr;
+    if (timing_on()) return KF_ERR_ARG;
+    if (!models || nmodels < 1 || nseq < 1 || !offsets || offsets[0] != 0) return KF_ERR_ARG;
+    for (int s = 0; s < nseq; ++s)
+        if (offsets[s + 1] < offsets[s]) return KF_ERR_ARG;
+    const size_t need = kf_batch_workspace_size(op, models[0].nx, models[0].ny, offsets[nseq], nseq, nmodels, prec,
+                                                loglik != nullptr);
+    if (need == 0) return KF_ERR_ARG;
+    kf_batch_graph *g = new (std::nothrow) kf_batch_graph();
+    if (!g) return KF_ERR_OOM;
+    g->graph = nullptr;
+    g->exec = nullptr;
+    g->ws = nullptr;
+    for (int k = 0; k < KF_KERNEL_KINDS; ++k) g->kernels[k] = 0;
+    cudaStream_t st = nullptr;
+    kf_status_t s = from_cuda(cudaMalloc(&g->ws, need));
+    if (s == KF_OK) s = from_cuda(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    // a plain run stages the tables into the graph's workspace and loads the kernels
+    if (s == KF_OK)
+        s = run_batch(op, models, nmodels, model_of_seq, nseq, offsets, y, prec, m_out, P_out, loglik, g->ws, st, 0);
+    if (s == KF_OK) s = from_cuda(cudaStreamSynchronize(st));
+    if (s == KF_OK && kf_sync_status(st) != KF_OK) s = KF_ERR_TIMEOUT;
+    if (s == KF_OK) {
+        s = from_cuda(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        if (s == KF_OK) {
+            int64_t before[KF_KERNEL_KINDS];
+            for (int k = 0; k < KF_KERNEL_KINDS; ++k) before[k] = g_launches[k].load();
+            const kf_status_t sr = run_batch(op, models, nmodels, model_of_seq, nseq, offsets, y, prec, m_out, P_out,
+                                             loglik, g->ws, st, 1);
+            const kf_status_t se = from_cuda(cudaStreamEndCapture(st, &g->graph));
+            s = (sr != KF_OK) ? sr : se;
+            // the captured kernels did not run: count them at each replay instead
+            for (int k = 0; k < KF_KERNEL_KINDS; ++k) {
+                g->kernels[k] = g_launches[k].load() - before[k];
+                count_launches(k, int(-g->kernels[k]));
+            }
+        }
+    }
+    if (s == KF_OK) s = from_cuda(cudaGraphInstantiate(&g->exec, g->graph, 0));
+    if (st) cudaStreamDestroy(st);
+    if (s != KF_OK) {
+        kf_batch_graph_destroy(g);
+        return s;
+    }
+    *graph = g;
+    return KF_OK;
+}
+
+kf_status_t kf_batch_graph_launch(kf_batch_graph_t *graph, void *stream) {
+    if (!graph || !graph->exec) return KF_ERR_ARG;
+    const kf_status_t s = from_cuda(cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)));
+    if (s == KF_OK)
+        for (int k = 0; k < KF_KERNEL_KINDS; ++k) count_launches(k, int(graph->kernels[k]));
+    return s;
+}
+
+kf_status_t kf_batch_graph_destroy(kf_batch_graph_t *graph) {
+    if (!graph) return KF_OK;
+    if (graph->exec) cudaGraphExecDestroy(graph->exec);
+    if (graph->graph) cudaGraphDestroy(graph->graph);
+    if (graph->ws) cudaFree(graph->ws);
+    delete graph;
+    return KF_OK;
 }
 
 kf_status_t kf_rts_smooth_noalloc(const kf_model_t *model, int64_t T, const void *y, kf_precision_t prec,

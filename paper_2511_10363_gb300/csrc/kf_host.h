@@ -65,6 +65,7 @@ struct BatchReq {
     const int *model_of;        // host [nseq]
     const HostModel *hms;       // host [nmodels]
     int all_ny_half;            // every model has ny = nx / 2
+    int params_resident;        // the tables are already in the workspace (graph capture)
 };
 
 bool debug_on();   // KFSCAN_DEBUG set in the environment

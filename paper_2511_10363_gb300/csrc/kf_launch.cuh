@@ -601,22 +601,26 @@ static cudaError_t launch_batch_typed(const LaunchReq &q, const BatchReq &b) {
     const WsLayout L = ws_layout<N, R>(q.op, KF_SCAN_DLB_I, q.T);
     const BatchLayout B = batch_layout<N, R>(q.op, q.T, b.nseq, b.nmodels, q.loglik != nullptr);
     char *ws = static_cast<char *>(q.ws);
-    // stage the per-model constants, offsets and model indices into the workspace
-    FiltParams<N, R> *hp = static_cast<FiltParams<N, R> *>(malloc(sizeof(FiltParams<N, R>) * size_t(b.nmodels)));
-    if (!hp) return cudaErrorMemoryAllocation;
-    for (int i = 0; i < b.nmodels; ++i) to_params<N, R>(b.hms[i], hp[i]);
-    cudaError_t e = cudaMemcpyAsync(ws + B.params, hp, sizeof(FiltParams<N, R>) * size_t(b.nmodels),
-                                    cudaMemcpyHostToDevice, q.stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ws + B.offsets, b.offsets, sizeof(int64_t) * (size_t(b.nseq) + 1), cudaMemcpyHostToDevice,
+    // stage the per-model constants, offsets and model indices into the
+    // workspace (a graph capture finds them there already)
+    cudaError_t e = cudaSuccess;
+    if (!b.params_resident) {
+        FiltParams<N, R> *hp = static_cast<FiltParams<N, R> *>(malloc(sizeof(FiltParams<N, R>) * size_t(b.nmodels)));
+        if (!hp) return cudaErrorMemoryAllocation;
+        for (int i = 0; i < b.nmodels; ++i) to_params<N, R>(b.hms[i], hp[i]);
+        e = cudaMemcpyAsync(ws + B.params, hp, sizeof(FiltParams<N, R>) * size_t(b.nmodels), cudaMemcpyHostToDevice,
                             q.stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ws + B.model_of, b.model_of, sizeof(int) * size_t(b.nseq), cudaMemcpyHostToDevice,
-                            q.stream);
-    // the sources are pageable: each copy has been staged when it returns,
-    // so the host buffers may be released right away
-    free(hp);
-    if (e != cudaSuccess) return e;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws + B.offsets, b.offsets, sizeof(int64_t) * (size_t(b.nseq) + 1),
+                                cudaMemcpyHostToDevice, q.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws + B.model_of, b.model_of, sizeof(int) * size_t(b.nseq), cudaMemcpyHostToDevice,
+                                q.stream);
+        // the sources are pageable: each copy has been staged when it
+        // returns, so the host buffers may be released right away
+        free(hp);
+        if (e != cudaSuccess) return e;
+    }
     Src src;
     src.prm = reinterpret_cast<const FiltParams<N, R> *>(ws + B.params);
     src.model_of = reinterpret_cast<const int *>(ws + B.model_of);

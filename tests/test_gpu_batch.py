@@ -125,3 +125,37 @@ def test_batch_argument_errors():
         kf.kf_batch_smooth("rts", model, [1, 10], y, "fp32")             # offsets[0] != 0
     with pytest.raises(kf.KfError):
         kf.kf_batch_smooth("rts", model, [0, 4, 10], y, "fp32", model_of=[0, 3])   # bad model index
+
+
+@pytest.mark.parametrize("op", ["filter", "rts", "tf"])
+def test_batch_graph(op):
+    """The batched call captured in a CUDA graph gives the same results as
+    kf_batch_smooth, also after new measurements are written into y."""
+    import torch
+    import paper_2511_10363_gb300 as kf
+    rng = np.random.default_rng(31)
+    lengths = np.concatenate([[5, 0, 1], rng.integers(50, 3000, size=20)])
+    model = W.cv_model()
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    y1, _ = W.ragged_batch(model, lengths, seed=32)
+    y2, _ = W.ragged_batch(model, lengths, seed=33)
+    yt = torch.tensor(y1, dtype=torch.float32, device="cuda")
+    g = kf.BatchGraph(op, model, offs, yt, "fp32", loglik=True)
+    try:
+        for ynew in (y1, y2, y1):
+            yt.copy_(torch.tensor(ynew, dtype=torch.float32))
+            m, P, ll = g.launch()
+            torch.cuda.synchronize()
+            assert kf.kf_sync_status() == 0
+            rm, rP, rll = kf.kf_batch_smooth(op, model, offs, yt, "fp32", loglik=True)
+            torch.cuda.synchronize()
+            # the look-back may combine in a different order from run to run
+            # (whichever predecessor has published first): equal up to FP32 rounding
+            rm_, rP_ = rm.double().cpu().numpy(), rP.double().cpu().numpy()
+            assert mean_err(m.double().cpu().numpy(), rm_, rP_) <= TOL["fp32"]
+            assert cov_err(P.double().cpu().numpy(), rP_) <= TOL["fp32"]
+            assert np.allclose(ll.cpu().numpy(), rll.cpu().numpy(), rtol=1e-5, atol=1e-3)
+        # and against the oracle on the last data
+        check_against_oracle(op, [model], None, lengths, y1, "fp32")
+    finally:
+        g.close()
