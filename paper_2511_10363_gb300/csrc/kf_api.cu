@@ -355,6 +355,92 @@ static kf_status_t library_workspace(size_t bytes, void **out) {
     return KF_OK;
 }
 
+// ---------------------------------------------------------------- tile-scan table cache
+
+// 32 slots of 32 KB per device, allocated on first use, least recently
+// used slot replaced; an event per slot marks the last launch that reads it.
+namespace {
+constexpr int TSC_SLOTS = 32;
+constexpr size_t TSC_SLOT_BYTES = 32 << 10;
+struct TscSlot {
+    uint64_t key;
+    uint64_t stamp;
+    bool valid;
+    cudaEvent_t last_use;
+};
+struct TscDev {
+    char *base = nullptr;
+    bool failed = false;
+    TscSlot slot[TSC_SLOTS];
+};
+std::mutex g_tsc_mu;
+TscDev g_tsc[64];
+uint64_t g_tsc_clock = 0;
+
+TscDev *tsc_dev(int *dev_out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    TscDev &d = g_tsc[dev];
+    if (d.failed) return nullptr;
+    if (!d.base) {
+        if (cudaMalloc(&d.base, TSC_SLOTS * TSC_SLOT_BYTES) != cudaSuccess) {
+            d.base = nullptr;
+            d.failed = true;
+            return nullptr;
+        }
+        for (int i = 0; i < TSC_SLOTS; ++i) {
+            d.slot[i].valid = false;
+            d.slot[i].stamp = 0;
+            if (cudaEventCreateWithFlags(&d.slot[i].last_use, cudaEventDisableTiming) != cudaSuccess) d.failed = true;
+        }
+        if (d.failed) return nullptr;
+    }
+    *dev_out = dev;
+    return &d;
+}
+}  // namespace
+
+const void *scan_table_lookup(uint64_t key, int *slot) {
+    std::lock_guard<std::mutex> lk(g_tsc_mu);
+    int dev = 0;
+    TscDev *d = tsc_dev(&dev);
+    if (!d) return nullptr;
+    for (int i = 0; i < TSC_SLOTS; ++i)
+        if (d->slot[i].valid && d->slot[i].key == key) {
+            d->slot[i].stamp = ++g_tsc_clock;
+            *slot = dev * TSC_SLOTS + i;
+            return d->base + size_t(i) * TSC_SLOT_BYTES;
+        }
+    return nullptr;
+}
+
+const void *scan_table_insert(uint64_t key, const void *host, size_t bytes, cudaStream_t st, int *slot) {
+    if (bytes > TSC_SLOT_BYTES) return nullptr;
+    std::lock_guard<std::mutex> lk(g_tsc_mu);
+    int dev = 0;
+    TscDev *d = tsc_dev(&dev);
+    if (!d) return nullptr;
+    int v = 0;
+    for (int i = 1; i < TSC_SLOTS; ++i)
+        if (!d->slot[i].valid || (d->slot[v].valid && d->slot[i].stamp < d->slot[v].stamp)) v = i;
+    if (d->slot[v].valid && cudaEventSynchronize(d->slot[v].last_use) != cudaSuccess) return nullptr;
+    char *dst = d->base + size_t(v) * TSC_SLOT_BYTES;
+    // pageable source: the copy has been staged when the call returns
+    if (cudaMemcpyAsync(dst, host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return nullptr;
+    d->slot[v].key = key;
+    d->slot[v].valid = true;
+    d->slot[v].stamp = ++g_tsc_clock;
+    *slot = dev * TSC_SLOTS + v;
+    return dst;
+}
+
+void scan_table_used(int slot, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_tsc_mu);
+    const int dev = slot / TSC_SLOTS, i = slot % TSC_SLOTS;
+    if (dev < 0 || dev >= 64 || !g_tsc[dev].base) return;
+    cudaEventRecord(g_tsc[dev].slot[i].last_use, st);
+}
+
 static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // Rows of `len` values of w bytes move as the widest of 16-, 8- and 4-byte
@@ -683,6 +769,7 @@ static kf_status_t rts_noalloc(const kf_model_t *md, int64_t T, const void *y, k
     q.threads = int(g_opt[KF_OPT_THREADS].load());
     q.no_lowrank = int(g_opt[KF_OPT_GENERAL_SOLVE].load());
     q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
+    q.no_alloc = 1;
     // the status word must start at zero (the scans' descriptors are cleared per launch)
     cudaError_t e = cudaMemsetAsync(q.status, 0, sizeof(int), q.stream);
     if (e != cudaSuccess) return from_cuda(e);

@@ -55,7 +55,16 @@ struct LaunchReq {
     int no_lowrank;      // 1: use the general Lemma 1 solve even when ny = nx / 2
     int lookback_warps;  // warps of a CTA that take part in the look-back (0: all)
     double *ll_step;     // per-step log-likelihood terms (batched calls; set by the batch launcher)
+    int no_alloc;        // the call may not allocate: no device table cache
 };
+
+// Device cache of tile-scan tables (kf_api.cu): a table is found by its key,
+// or inserted (copied from host memory on `st`); scan_table_used records that
+// a launch on `st` reads slot `slot`, so that the slot is not overwritten
+// before that launch has finished.  Both return null when unavailable.
+const void *scan_table_lookup(uint64_t key, int *slot);
+const void *scan_table_insert(uint64_t key, const void *host, size_t bytes, cudaStream_t st, int *slot);
+void scan_table_used(int slot, cudaStream_t st);
 
 // A batch of sequences concatenated in y: sequence s covers
 // [offsets[s], offsets[s+1]) and uses model hms[model_of[s]].

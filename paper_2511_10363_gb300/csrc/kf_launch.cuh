@@ -4,6 +4,7 @@
 
 #include "kf_host.h"
 #include <math.h>
+#include <mutex>
 #include <stdio.h>
 
 #include "scan_levels.cuh"
@@ -112,7 +113,7 @@ static inline void host_mm(const double *a, const double *b, int n, int p, int q
 // J_{c+1} = A_c^T (I + J C_c)^{-1} J A_c + J_c.  Leaves t.K = 0 when K is
 // outside the table.
 template <int N, int M, typename R>
-static void build_fold_table(const HostModel &h, int K, FoldTab<N, M, R> &t) {
+static void build_fold_table(const HostModel &h, int K, FoldTab<N, M, R> &t, double *agg64 = nullptr) {
     using TT = FoldTab<N, M, R>;
     t.K = 0;
     if (K < 2 || K - 1 > TT::KT || h.n != N || h.m != M) return;
@@ -166,6 +167,12 @@ static void build_fold_table(const HostModel &h, int K, FoldTab<N, M, R> &t) {
             t.C[su(N, r, c)] = R(0.5 * (Ci[r * N + c] + Ci[c * N + r]));
             t.J[su(N, r, c)] = R(0.5 * (Ji[r * N + c] + Ji[c * N + r]));
         }
+    if (agg64)   // FP64 (A, C, J) of the K-element aggregate, full matrices
+        for (int i = 0; i < NN; ++i) {
+            agg64[i] = Ai[i];
+            agg64[NN + i] = 0.5 * (Ci[i] + Ci[(i % N) * N + i / N]);
+            agg64[2 * NN + i] = 0.5 * (Ji[i] + Ji[(i % N) * N + i / N]);
+        }
     // the run from a_1: C'_1 = C_1, C'_{c+1} = T1'_c C'_c A^T + C (the filtering covariances)
     for (int i = 0; i < NN; ++i) Ci[i] = h.C1[i];
     for (int c = 1; c < K; ++c) {
@@ -185,12 +192,113 @@ static void build_fold_table(const HostModel &h, int K, FoldTab<N, M, R> &t) {
         for (int c = r; c < N; ++c) t.C1K[su(N, r, c)] = R(0.5 * (Ci[r * N + c] + Ci[c * N + r]));
     t.K = K;
 }
-static inline void build_fold_table(const HostModel &, int, NoTab &t) { t.K = 0; }
+static inline void build_fold_table(const HostModel &, int, NoTab &t, double * = nullptr) { t.K = 0; }
+
+// (A, C, J) half of Lemma 1 for x (x) y, full N x N matrices in FP64.
+template <int N>
+static bool host_acj_combine(const double *x, const double *y, double *o) {
+    constexpr int NN = N * N;
+    const double *Ax = x, *Cx = x + NN, *Jx = x + 2 * NN, *Ay = y, *Cy = y + NN, *Jy = y + 2 * NN;
+    double X[NN], T1[NN], W[NN], AyT[NN], T3[NN], V[NN];
+    if (!host_inv_I_plus(Cx, Jy, N, X)) return false;
+    host_mm(Ay, X, N, N, N, T1);                       // Ay X
+    host_mm(T1, Ax, N, N, N, o);                       // A = Ay X Ax
+    host_mm(T1, Cx, N, N, N, W);                       // Ay X Cx
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) AyT[r * N + c] = Ay[c * N + r];
+    host_mm(W, AyT, N, N, N, o + NN);                  // C = Ay X Cx Ay^T + Cy
+    for (int i = 0; i < NN; ++i) o[NN + i] += Cy[i];
+    for (int r = 0; r < N; ++r)                        // T3 = Ax^T X^T
+        for (int c = 0; c < N; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < N; ++k) s += Ax[k * N + r] * X[c * N + k];
+            T3[r * N + c] = s;
+        }
+    host_mm(T3, Jy, N, N, N, V);                       // J = Ax^T X^T Jy Ax + Jx
+    host_mm(V, Ax, N, N, N, o + 2 * NN);
+    for (int i = 0; i < NN; ++i) o[2 * NN + i] += Jx[i];
+    for (int i = 0; i < NN; ++i) {                     // symmetric parts exactly symmetric
+        const int r = i / N, c = i % N;
+        if (c < r) {
+            o[NN + i] = o[NN + c * N + r] = 0.5 * (o[NN + i] + o[NN + c * N + r]);
+            o[2 * NN + i] = o[2 * NN + c * N + r] = 0.5 * (o[2 * NN + i] + o[2 * NN + c * N + r]);
+        }
+    }
+    return true;
+}
+
+// Coefficients (M1 | M2 | M3 | M4) of a left span (A,C,J)_p and a right span
+// (A,C,J)_q (ScanTab), rounded to R.
+template <int N, typename R>
+static bool host_scan_coeffs(const double *left, const double *right, R *w) {
+    constexpr int NN = N * N;
+    const double *Ap = left, *Cp = left + NN, *Aq = right, *Jq = right + 2 * NN;
+    double X[NN], M1[NN], M2[NN], M3[NN], M4[NN];
+    if (!host_inv_I_plus(Cp, Jq, N, X)) return false;
+    host_mm(Aq, X, N, N, N, M1);
+    host_mm(M1, Cp, N, N, N, M2);
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < N; ++k) s += Ap[k * N + r] * X[c * N + k];
+            M3[r * N + c] = s;
+        }
+    host_mm(M3, Jq, N, N, N, M4);
+    for (int i = 0; i < NN; ++i) {
+        w[i] = R(M1[i]);
+        w[NN + i] = R(M2[i]);
+        w[2 * NN + i] = R(M3[i]);
+        w[3 * NN + i] = R(M4[i]);
+    }
+    return true;
+}
+
+// The tile-scan table (ScanTab) from the FP64 (A, C, J) of one thread's
+// K-element aggregate, for CTAs of nw warps.
+template <int N, typename R>
+static bool build_scan_table(const double *chunk, int nw, R *out) {
+    using T = ScanTab<N, R>;
+    constexpr int NN = N * N, E3 = 3 * NN;
+    if (nw > T::NWARPS) return false;
+    static thread_local double pw[32 + T::NWARPS][3 * NN];   // spans 1..32, then 64, 96, ...
+    auto span = [&](int c) -> double * { return c <= 32 ? pw[c - 1] : pw[32 + c / 32 - 2]; };
+    for (int i = 0; i < E3; ++i) pw[0][i] = chunk[i];
+    for (int c = 1; c < 32; ++c)
+        if (!host_acj_combine<N>(span(c), span(1), span(c + 1))) return false;
+    for (int w = 1; w < nw; ++w)
+        if (!host_acj_combine<N>(span(32 * w), span(32), span(32 * (w + 1)))) return false;
+    for (int s = 1; s <= 16; s <<= 1)
+        for (int p = 1; p <= s; ++p)
+            if (!host_scan_coeffs<N, R>(span(p), span(s), out + T::w_off(s, p))) return false;
+    for (int s = 1; s < nw; s <<= 1)
+        for (int p = 1; p <= s; ++p)
+            if (!host_scan_coeffs<N, R>(span(32 * p), span(32 * s), out + T::v_off(s, p))) return false;
+    auto put = [&](int c) {
+        const double *x = span(c);
+        R *o = out + T::pw_off(c);
+        for (int i = 0; i < NN; ++i) o[i] = R(x[i]);
+        for (int r = 0; r < N; ++r)
+            for (int q = r; q < N; ++q) {
+                o[NN + su(N, r, q)] = R(x[NN + r * N + q]);
+                o[NN + T::S + su(N, r, q)] = R(x[2 * NN + r * N + q]);
+            }
+    };
+    for (int c = 1; c <= 32; ++c) put(c);
+    for (int w = 2; w <= nw; ++w) put(32 * w);
+    return true;
+}
+
+// FNV-1a over bytes
+static inline uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
 
 // ---------------------------------------------------------------- tile plan
 
 template <class P, int THREADS, int V, int C>
-static int max_resident_tiles(int device, int smem) {
+static int max_resident_tiles_query(int device, int smem) {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (debug_on()) {
@@ -205,6 +313,28 @@ static int max_resident_tiles(int device, int smem) {
     if (debug_on()) fprintf(stderr, "[kfscan] occupancy: %d per_sm=%d sms=%d\n", int(oe), per_sm, sms);
     if (per_sm < 1) per_sm = 1;
     return sms * per_sm;
+}
+
+// The occupancy query, once per kernel, device and shared-memory size (it
+// costs microseconds of host time per launch otherwise).
+template <class P, int THREADS, int V, int C>
+static int max_resident_tiles(int device, int smem) {
+    static std::mutex mu;
+    static int dev_of[16], smem_of[16], val_of[16], n = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (int i = 0; i < n; ++i)
+            if (dev_of[i] == device && smem_of[i] == smem) return val_of[i];
+    }
+    const int v = max_resident_tiles_query<P, THREADS, V, C>(device, smem);
+    std::lock_guard<std::mutex> lk(mu);
+    if (n < 16) {
+        dev_of[n] = device;
+        smem_of[n] = smem;
+        val_of[n] = v;
+        ++n;
+    }
+    return v;
 }
 
 struct TilePlan {
@@ -296,7 +426,7 @@ constexpr int stage_buf_bytes() {
 }
 template <class P, int C>
 constexpr int stage_bytes_warp() {   // one warp
-    constexpr int in = 2 * stage_buf_bytes<P, C, P::IN_REC>();
+    constexpr int in = stage_nst<P>() * ((stage_buf_bytes<P, C, P::IN_REC>() + 15) & ~15);
     constexpr int o1 = stage_buf_bytes<P, C, P::O1>(), o2 = stage_buf_bytes<P, C, P::O2>(),
                   o3 = stage_buf_bytes<P, C, P::O3>();
     if constexpr (P::KIND == 0) return in + (o1 > o2 + o3 ? o1 : o2 + o3);
@@ -330,7 +460,7 @@ static void stage_layout(const typename P::Args &args, DlbCtl &ctl) {
     bool use_in = P::IN_REC != 0, use_out[3];
     for (int i = 0; i < 3; ++i) use_out[i] = recs[i] && P::out_arr(args, i);
     auto need = [&]() {
-        int b = use_in ? 2 * ((in_bytes + 15) & ~15) : 0;
+        int b = use_in ? stage_nst<P>() * ((in_bytes + 15) & ~15) : 0;
         for (int i = 0; i < 3; ++i) b += use_out[i] ? (sizes[i] + 15) & ~15 : 0;
         return b * NW + P::tab_bytes();
     };
@@ -348,10 +478,11 @@ static void stage_layout(const typename P::Args &args, DlbCtl &ctl) {
         o += (bytes + 15) & ~15;
         return at;
     };
-    ctl.sm_in0 = ctl.sm_in1 = -1;
+    ctl.sm_in0 = -1;
+    ctl.sm_in_stride = (in_bytes + 15) & ~15;
     if (use_in) {
         ctl.sm_in0 = take(in_bytes);
-        ctl.sm_in1 = take(in_bytes);
+        for (int k = 1; k < stage_nst<P>(); ++k) take(in_bytes);
     }
     for (int i = 0; i < 3; ++i) ctl.sm_out[i] = use_out[i] ? take(sizes[i]) : -1;
     ctl.sm_warp = o;
@@ -383,9 +514,27 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
     }
     const TilePlan tp =
         plan_tiles(total, THREADS, THREADS * V, max_resident_tiles<P, THREADS, V, C>(dev, smem), q.k_override);
+    ctl.tsc = nullptr;
+    int tsc_slot = -1;
     if constexpr (P::TABLE) {
-        build_fold_table(*q.hm, tp.K, a2.tab);
+        using ST = ScanTab<P::NX, typename P::R>;
+        double chunk[3 * P::NX * P::NX] = {};
+        build_fold_table(*q.hm, tp.K, a2.tab, chunk);
         if (a2.tab.K == 0) ctl.sm_tab = -1;
+        // tile-scan table: cached on the device by its key (the fold table
+        // and the CTA size determine it)
+        if (sizeof(typename P::R) == 8 && a2.tab.K != 0 && !q.no_alloc) {
+            const int id[2] = {THREADS, int(sizeof(typename P::R))};
+            uint64_t key = fnv1a(chunk, sizeof(chunk));
+            key = fnv1a(id, sizeof(id), key);
+            const void *d = scan_table_lookup(key, &tsc_slot);
+            if (!d) {
+                static thread_local typename P::R host[ST::SIZE];
+                if (build_scan_table<P::NX, typename P::R>(chunk, THREADS / 32, host))
+                    d = scan_table_insert(key, host, sizeof(host), q.stream, &tsc_slot);
+            }
+            ctl.tsc = d;
+        }
     }
     ctl.counters = reinterpret_cast<int *>(ws + ctl_off);
     ctl.flags = ctl.counters + 2;
@@ -412,6 +561,7 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
     if (timing_on()) timing_record(P::KIND, q.stream, &t0);
     dlb_scan_kernel<P, THREADS, V, C><<<tp.ntiles, THREADS, smem, q.stream>>>(a2, ctl);
     e = cudaGetLastError();
+    if (ctl.tsc) scan_table_used(tsc_slot, q.stream);
     count_launches(P::KIND, 1);
     if (t0) timing_commit(P::KIND, q.stream, t0);
     if (debug_on()) {

@@ -232,11 +232,81 @@ struct NoTab {
     int K;
 };
 
+// Tile-scan table.  In a tile where every thread folded K fresh elements
+// (the table fold above), every thread aggregate has the same (A, C, J), the
+// K-element aggregate; so has every run of c consecutive thread aggregates,
+// its c-th power under Lemma 1.  The warp scan (Kogge-Stone, offsets
+// s = 1..16) and the scan of the warp aggregates (offsets s = 1..4, spans of
+// 32 threads) then combine a left span of p with a right span of s thread
+// aggregates, and Lemma 1 reduces to
+//   b   <- M1 b_x + M2 eta_y + b_y,      M1 = A_s X,  M2 = A_s X C_p,
+//   eta <- eta_x + M3 eta_y - M4 b_x,    M3 = A_p^T X^T,  M4 = M3 J_s,
+// X = (I + C_p J_s)^{-1} (x the left, y the right operand).  The host
+// computes, in FP64: W(s, p) for the warp scan, V(s, p) for the warp
+// aggregates, and the (A, C, J) of spans 1..32 and 32 w (w <= 8 warps),
+// which complete the exclusive prefixes and the tile aggregate into
+// elements.
+template <int N, typename R>
+struct ScanTab {
+    static constexpr int NN = N * N, S = N * (N + 1) / 2;
+    static constexpr int WE = 4 * NN;        // M1 | M2 | M3 | M4, row-major
+    static constexpr int PE = NN + 2 * S;    // A | C | J (packed)
+    static constexpr int NWARPS = 8, NWE = 31, NVE = 7, NPW = 32 + NWARPS - 1;
+    static constexpr int SIZE = (NWE + NVE) * WE + NPW * PE;
+    static KF_HD int w_off(int s, int p) { return (s + p - 2) * WE; }
+    static KF_HD int v_off(int s, int p) { return (NWE + s + p - 2) * WE; }
+    static KF_HD int pw_off(int c) { return (NWE + NVE) * WE + (c <= 32 ? c - 1 : 32 + c / 32 - 2) * PE; }
+};
+
+// One table-driven combine of (b, eta) halves: (bx, ex) the left operand,
+// (b, e) the right one and the result.
+template <int N, typename R>
+KF_D void tsc_combine(const R *w, const R *bx, const R *ex, R *b, R *e) {
+    constexpr int NN = N * N;
+    R nb[N], ne[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        R sb = b[r], se = ex[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            sb += __ldg(w + r * N + k) * bx[k] + __ldg(w + NN + r * N + k) * e[k];
+            se += __ldg(w + 2 * NN + r * N + k) * e[k] - __ldg(w + 3 * NN + r * N + k) * bx[k];
+        }
+        nb[r] = sb;
+        ne[r] = se;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        b[r] = nb[r];
+        e[r] = ne[r];
+    }
+}
+
+// The element of a span of c thread aggregates with halves (b, eta).
+template <int N, typename R>
+KF_D void tsc_elem(const R *tab, int c, const R *b, const R *eta, FElem<N, R> &el) {
+    using T = ScanTab<N, R>;
+    using E = FElem<N, R>;
+    const R *pw = tab + T::pw_off(c);
+#pragma unroll
+    for (int i = 0; i < T::NN; ++i) el.v[E::oA + i] = __ldg(pw + i);
+#pragma unroll
+    for (int i = 0; i < T::S; ++i) {
+        el.v[E::oC + i] = __ldg(pw + T::NN + i);
+        el.v[E::oJ + i] = __ldg(pw + T::NN + T::S + i);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        el.v[E::ob + i] = b[i];
+        el.v[E::oe + i] = eta[i];
+    }
+}
+
 // LR > 0: every fresh element's J is U^T U of rank LR = ny, and the thread
 // fold and the carry pass use the low-rank forms (kf_math.cuh).
 template <int N, typename Rt, int MODE, class Src, int LR = 0>
 struct FilterFwd {
-    static constexpr int KIND = 0;
+    static constexpr int KIND = 0, NX = N;
     static constexpr bool REV = false;
     using R = Rt;
     using Elem = FElem<N, R>;

@@ -46,10 +46,12 @@ struct DlbCtl {
     int K;                 // positions per thread
     int inject_skip_tile;  // test hook: this tile never publishes (-1: none)
     // per-warp dynamic shared memory: byte offsets of the staging buffers
-    // (input double buffer, three outputs; -1 = not staged: the records are
-    // read or written in place) and the warp stride
-    int sm_in0, sm_in1, sm_out[3], sm_warp;
+    // (the first of stage_nst input buffers and their stride, three outputs;
+    // -1 = not staged: the records are read or written in place) and the
+    // warp stride
+    int sm_in0, sm_in_stride, sm_out[3], sm_warp;
     int sm_tab;            // byte offset of the fold-table rows (-1: none)
+    const void *tsc;       // tile-scan table (ScanTab) in device memory, or null
     int lbw;               // warps that take part in the look-back (1 .. THREADS/32)
     uint64_t *trace;       // optional [ntiles][8] %globaltimer stamps at phase boundaries
     int trace_cap;         // tiles the trace buffer holds
@@ -211,9 +213,11 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
     const int64_t end = start + ctl.K < total ? start + ctl.K : total;
 
     unsigned char *wsm = dsm + warp * ctl.sm_warp;
-    // staged input (null: the records are read in place)
+    // staged input ring (null: the records are read in place)
+    constexpr int NST = stage_nst<P>();
+    constexpr int IRC = P::IN_REC > 0 ? P::IN_REC : 1;
     unsigned char *const in0 = (P::IN_REC && ctl.sm_in0 >= 0) ? wsm + ctl.sm_in0 : nullptr;
-    unsigned char *const in1 = (P::IN_REC && ctl.sm_in1 >= 0) ? wsm + ctl.sm_in1 : nullptr;
+    auto inbuf = [&](int ch) { return in0 + (ch % NST) * ctl.sm_in_stride; };
     const int nchunks = (ctl.K + C - 1) / C;
     const R *in_arr = P::in_arr(args);
 
@@ -226,19 +230,20 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
         if constexpr (P::TABLE) tf.c = 0;
         SegCursor cur = P::cursor(args, start < total ? start : total - 1);
         if (P::IN_REC > 0 && in0) {
-            stage_load<C, (P::IN_REC > 0 ? P::IN_REC : 1)>(in_arr, seg_first<P, C>(total, start0), dK, total, in0, lane);
-            cp_async_commit();
+#pragma unroll
+            for (int k = 0; k < NST - 1; ++k) {
+                if (k < nchunks)
+                    stage_load<C, IRC>(in_arr, seg_first<P, C>(total, start0 + k * C), dK, total, inbuf(k), lane);
+                cp_async_commit();
+            }
         }
         for (int ch = 0; ch < nchunks; ++ch) {
             if (P::IN_REC > 0 && in0) {
-                if (ch + 1 < nchunks) {
-                    stage_load<C, (P::IN_REC > 0 ? P::IN_REC : 1)>(in_arr, seg_first<P, C>(total, start0 + (ch + 1) * C), dK, total,
-                                             ((ch + 1) & 1) ? in1 : in0, lane);
-                    cp_async_commit();
-                    cp_async_wait<1>();
-                } else {
-                    cp_async_wait<0>();
-                }
+                const int ahead = ch + NST - 1;   // its buffer was last read by chunk ch - 1
+                if (ahead < nchunks)
+                    stage_load<C, IRC>(in_arr, seg_first<P, C>(total, start0 + ahead * C), dK, total, inbuf(ahead), lane);
+                cp_async_commit();
+                cp_async_wait<NST - 1>();   // chunk ch has arrived
                 __syncwarp();
             }
 #pragma unroll 1
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
                 const int64_t p = start + ch * C + c;
                 if (p >= end) break;
                 const R *in = !P::IN_REC ? nullptr
-                              : in0 ? stage_rec<C, P::IN_REC, R>((ch & 1) ? in1 : in0, lane, seg_slot<P, C>(c))
+                              : in0 ? stage_rec<C, P::IN_REC, R>(inbuf(ch), lane, seg_slot<P, C>(c))
                                     : in_arr + gidx<P>(total, p) * P::IN_REC;
                 if constexpr (P::TABLE) {
                     if (fast) {
@@ -273,54 +278,150 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
     }
 
     // ---- 3. warp scan, warp-aggregate scan (cold: kept rolled for code size)
-#pragma unroll 1
-    for (int s = 1; s < 32; s <<= 1) {
-        Elem o, t;
-        shfl_up_x(agg, o, s);
-        if (lane >= s) {
-            P::combine(o, agg, t);
-            agg = t;
-        }
+    // FP64: a tile whose threads all folded K fresh elements scans only the
+    // (b, eta) halves, with the tile-scan table (ScanTab), which replaces
+    // Lemma 1 on the slow FP64 pipe by four matrix-vector products.  (In FP32
+    // the table's loads cost as much as the combines they save.)
+    bool tscan = false;
+    if constexpr (P::TABLE) {
+        tscan = sizeof(R) == 8 && ctl.tsc && tab && args.tab.K == ctl.K && tile > 0 && NW <= 8 &&
+                (int64_t(tile) + 1) * THREADS * ctl.K <= total;
     }
     Elem lex;
-    shfl_up_x(agg, lex, 1);
-    if (lane == 31) {
+    if constexpr (P::TABLE) {
+        if (tscan) {
+            constexpr int N = P::NX;
+            using ST = ScanTab<N, R>;
+            const R *tsc = static_cast<const R *>(ctl.tsc);
+            R b[N], e[N];
 #pragma unroll
-        for (int i = 0; i < ES; ++i) s_wx[warp][i] = agg.v[i];
-    }
-    __syncthreads();
-    if (trace) trace[1] = global_ns();
-    if (warp == 0) {
-        Elem w;
-        if (lane < NW) {
-#pragma unroll
-            for (int i = 0; i < ES; ++i) w.v[i] = s_wx[lane][i];
-        } else {
-            set_identity(w);
-        }
+            for (int i = 0; i < N; ++i) {
+                b[i] = agg.v[Elem::ob + i];
+                e[i] = agg.v[Elem::oe + i];
+            }
 #pragma unroll 1
-        for (int s = 1; s < NW; s <<= 1) {
+            for (int s = 1; s < 32; s <<= 1) {
+                R bx[N], ex[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    bx[i] = __shfl_up_sync(0xffffffffu, b[i], s);
+                    ex[i] = __shfl_up_sync(0xffffffffu, e[i], s);
+                }
+                if (lane >= s) {
+                    const int p = (lane - s + 1) < s ? (lane - s + 1) : s;
+                    tsc_combine<N, R>(tsc + ST::w_off(s, p), bx, ex, b, e);
+                }
+            }
+            R lb[N], le[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                lb[i] = __shfl_up_sync(0xffffffffu, b[i], 1);
+                le[i] = __shfl_up_sync(0xffffffffu, e[i], 1);
+            }
+            if (lane > 0) tsc_elem<N, R>(tsc, lane, lb, le, lex);
+            else set_identity(lex);
+            if (lane == 31) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    s_wx[warp][Elem::ob + i] = b[i];
+                    s_wx[warp][Elem::oe + i] = e[i];
+                }
+            }
+            __syncthreads();
+            if (trace) trace[1] = global_ns();
+            if (warp == 0) {
+                R wb[N], we[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    wb[i] = lane < NW ? s_wx[lane][Elem::ob + i] : R(0);
+                    we[i] = lane < NW ? s_wx[lane][Elem::oe + i] : R(0);
+                }
+#pragma unroll 1
+                for (int s = 1; s < NW; s <<= 1) {
+                    R bx[N], ex[N];
+#pragma unroll
+                    for (int i = 0; i < N; ++i) {
+                        bx[i] = __shfl_up_sync(0xffffffffu, wb[i], s);
+                        ex[i] = __shfl_up_sync(0xffffffffu, we[i], s);
+                    }
+                    if (lane >= s && lane < NW) {
+                        const int p = (lane - s + 1) < s ? (lane - s + 1) : s;
+                        tsc_combine<N, R>(tsc + ST::v_off(s, p), bx, ex, wb, we);
+                    }
+                }
+                R xb[N], xe[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    xb[i] = __shfl_up_sync(0xffffffffu, wb[i], 1);
+                    xe[i] = __shfl_up_sync(0xffffffffu, we[i], 1);
+                }
+                __syncwarp();
+                if (lane < NW) {
+                    Elem wx;
+                    if (lane == 0) set_identity(wx);
+                    else tsc_elem<N, R>(tsc, 32 * lane, xb, xe, wx);
+#pragma unroll
+                    for (int i = 0; i < ES; ++i) s_wx[lane][i] = wx.v[i];
+                }
+                if (lane == NW - 1) {
+                    Elem w;
+                    tsc_elem<N, R>(tsc, 32 * NW, wb, we, w);
+#pragma unroll
+                    for (int i = 0; i < ES; ++i) s_red[0][i] = w.v[i];
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (!tscan) {
+#pragma unroll 1
+        for (int s = 1; s < 32; s <<= 1) {
             Elem o, t;
-            shfl_up_x(w, o, s);
+            shfl_up_x(agg, o, s);
             if (lane >= s) {
-                P::combine(o, w, t);
-                w = t;
+                P::combine(o, agg, t);
+                agg = t;
             }
         }
-        Elem wx;
-        shfl_up_x(w, wx, 1);
-        if (lane == 0) set_identity(wx);
-        __syncwarp();
-        if (lane < NW) {
+        shfl_up_x(agg, lex, 1);
+        if (lane == 31) {
 #pragma unroll
-            for (int i = 0; i < ES; ++i) s_wx[lane][i] = wx.v[i];
+            for (int i = 0; i < ES; ++i) s_wx[warp][i] = agg.v[i];
         }
-        if (lane == NW - 1) {
+        __syncthreads();
+        if (trace) trace[1] = global_ns();
+        if (warp == 0) {
+            Elem w;
+            if (lane < NW) {
 #pragma unroll
-            for (int i = 0; i < ES; ++i) s_red[0][i] = w.v[i];
+                for (int i = 0; i < ES; ++i) w.v[i] = s_wx[lane][i];
+            } else {
+                set_identity(w);
+            }
+#pragma unroll 1
+            for (int s = 1; s < NW; s <<= 1) {
+                Elem o, t;
+                shfl_up_x(w, o, s);
+                if (lane >= s) {
+                    P::combine(o, w, t);
+                    w = t;
+                }
+            }
+            Elem wx;
+            shfl_up_x(w, wx, 1);
+            if (lane == 0) set_identity(wx);
+            __syncwarp();
+            if (lane < NW) {
+#pragma unroll
+                for (int i = 0; i < ES; ++i) s_wx[lane][i] = wx.v[i];
+            }
+            if (lane == NW - 1) {
+#pragma unroll
+                for (int i = 0; i < ES; ++i) s_red[0][i] = w.v[i];
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     Elem tagg;
 #pragma unroll
     for (int i = 0; i < ES; ++i) tagg.v[i] = s_red[0][i];
@@ -462,19 +563,20 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
 #pragma unroll
         for (int i = 0; i < 3; ++i) obuf[i] = (ctl.sm_out[i] >= 0 && oarr[i]) ? wsm + ctl.sm_out[i] : nullptr;
         if (P::IN_REC > 0 && in0) {
-            stage_load<C, (P::IN_REC > 0 ? P::IN_REC : 1)>(in_arr, seg_first<P, C>(total, start0), dK, total, in0, lane);
-            cp_async_commit();
+#pragma unroll
+            for (int k = 0; k < NST - 1; ++k) {
+                if (k < nchunks)
+                    stage_load<C, IRC>(in_arr, seg_first<P, C>(total, start0 + k * C), dK, total, inbuf(k), lane);
+                cp_async_commit();
+            }
         }
         for (int ch = 0; ch < nchunks; ++ch) {
             if (P::IN_REC > 0 && in0) {
-                if (ch + 1 < nchunks) {
-                    stage_load<C, (P::IN_REC > 0 ? P::IN_REC : 1)>(in_arr, seg_first<P, C>(total, start0 + (ch + 1) * C), dK, total,
-                                             ((ch + 1) & 1) ? in1 : in0, lane);
-                    cp_async_commit();
-                    cp_async_wait<1>();
-                } else {
-                    cp_async_wait<0>();
-                }
+                const int ahead = ch + NST - 1;
+                if (ahead < nchunks)
+                    stage_load<C, IRC>(in_arr, seg_first<P, C>(total, start0 + ahead * C), dK, total, inbuf(ahead), lane);
+                cp_async_commit();
+                cp_async_wait<NST - 1>();
                 __syncwarp();
             }
             R llc = 0;   // log-likelihood terms of this chunk, summed in the working precision
@@ -485,7 +587,7 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
                 const int slot = seg_slot<P, C>(cc);
                 const int64_t g = gidx<P>(total, p);
                 const R *in = !P::IN_REC ? nullptr
-                              : in0 ? stage_rec<C, P::IN_REC, R>((ch & 1) ? in1 : in0, lane, slot)
+                              : in0 ? stage_rec<C, P::IN_REC, R>(inbuf(ch), lane, slot)
                                     : in_arr + g * P::IN_REC;
                 R *o1 = obuf[0] ? stage_rec<C, (P::O1 ? P::O1 : 1), R>(obuf[0], lane, slot)
                                 : (P::O1 && oarr[0]) ? oarr[0] + g * P::O1 : nullptr;

@@ -27,6 +27,12 @@ struct RecGeom {
     static constexpr int RU = BYTES / U;                                          // units per record
 };
 
+// Depth of the input pipeline: a warp keeps NST - 1 chunks of input records
+// in flight while it computes on one (the forward pass reads small y
+// records; the reverse passes 64-byte filter records).
+template <class P>
+constexpr int stage_nst() { return P::KIND == 0 ? 4 : 3; }
+
 template <int C, int REC, typename R>
 struct WarpStage {
     using G = RecGeom<REC, R>;
