@@ -300,7 +300,7 @@ def _timed(fn, reps=12, drop=2):
 
 def workload_sweep(args):
     """T = 2^10 .. 2^22 on the tracking model, RTS smoother, every scan
-    algorithm, FP32 and FP64 (smoothed steps/s)."""
+    algorithm (and the autotuned choice), FP32 and FP64 (smoothed steps/s)."""
     import torch
     import paper_2511_10363_gb300 as kf
     model = W.cv_model()
@@ -312,7 +312,7 @@ def workload_sweep(args):
         dt = kf.dtype_of(prec)
         yall = torch.tensor(y64, dtype=dt, device="cuda")
         out[prec] = {}
-        for scan in ("dlb", "ladner_fischer", "blelloch", "hillis_steele"):
+        for scan in ("auto", "dlb", "ladner_fischer", "blelloch", "hillis_steele"):
             row = {}
             for e in range(10, 23):
                 T = 1 << e
@@ -320,11 +320,15 @@ def workload_sweep(args):
                 ms = torch.empty((T, 4), dtype=dt, device="cuda")
                 Ps = torch.empty((T, 4, 4), dtype=dt, device="cuda")
                 ws = torch.empty(kf.kf_workspace_size("rts", 4, 2, T, prec, scan), dtype=torch.uint8, device="cuda")
+                if scan == "auto":   # the library's autotuner picks the launch configuration for this T
+                    kf.kf_autotune("rts", model, y, prec, reps=3, workspace=ws)
                 ms_ = _timed(lambda: kf.kf_rts_smooth(mdl, y, prec, scan, ms_out=ms, Ps_out=Ps, workspace=ws))
                 assert kf.kf_sync_status() == 0
                 row[T] = {"ms": ms_, "steps_per_s": T / (ms_ * 1e-3)}
                 del ws
             out[prec][scan] = row
+    if args.save_tuning:   # the entries kf_autotune recorded for every (precision, T) of the sweep
+        kf.kf_tuning_save(args.save_tuning)
     print(json.dumps({"workload": "sweep", "metric": "smoothed steps/s", "unit": "smoothed steps/s",
                       "model": "2D constant-velocity tracking nx=4 ny=2", "op": "rts (filter + smoother)",
                       "timing": "median of 10 after 2 dropped runs (CUDA events)", "results": out}))

@@ -433,10 +433,11 @@ constexpr int stage_bytes_warp() {   // one warp
     else return in + o1 + o2 + o3;
 }
 // Upper bound of C per pass, measured on GB300 (T = 2^20 and 2^22, FP32,
-// nx = 4): the forward pass is fastest with up to 4 staged steps, the
-// reverse passes with at most 2 (3 or more cost the RTS pass 10-20%).
+// nx = 4, with the pipeline depths of stage_nst): the forward pass is
+// fastest with up to 4 staged steps per chunk, the reverse passes with 1
+// (3 or more cost the RTS pass 10-20%).
 #ifndef KF_STAGE_CMAX
-#define KF_STAGE_CMAX(kind) ((kind) == 0 ? 4 : 2)
+#define KF_STAGE_CMAX(kind) ((kind) == 0 ? 4 : 1)
 #endif
 template <class P, int THREADS, int C = KF_STAGE_CMAX(P::KIND)>
 constexpr int stage_chunk() {

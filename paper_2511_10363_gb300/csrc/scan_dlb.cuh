@@ -447,15 +447,29 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
         const bool lbthread = tid < lbt;
         int qloc = -1;
         if (lbthread) {
+            // all of this thread's flags are read at once (relaxed, in flight
+            // together); only the ones not yet set are then waited for, and
+            // one acquire fence orders the flags before the aggregate loads
+            // (vv <= 32: at most 1024 tiles over at least 32 threads)
+            unsigned pend = 0;
 #pragma unroll 1
             for (int v = 0; v < vv; ++v) {
                 const int q = tile - 1 - (tid * vv + v);
                 if (q >= 0) {
-                    const int f = wait_flag(ctl.flags + q, ctl);
-                    if (f == 0) s_abort = 1;
-                    if (f == 2 && q > qloc) qloc = q;
+                    const int f = ld_relaxed(ctl.flags + q);
+                    if (f == 0) pend |= 1u << v;
+                    else if (f == 2 && q > qloc) qloc = q;
                 }
             }
+#pragma unroll 1
+            for (int v = 0; v < vv; ++v) {
+                if (!((pend >> v) & 1u)) continue;
+                const int q = tile - 1 - (tid * vv + v);
+                const int f = wait_flag(ctl.flags + q, ctl);
+                if (f == 0) s_abort = 1;
+                if (f == 2 && q > qloc) qloc = q;
+            }
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
         }
         if (qloc >= 0) atomicMax(&s_qstar, qloc);
         __syncthreads();

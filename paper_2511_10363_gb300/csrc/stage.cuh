@@ -28,10 +28,15 @@ struct RecGeom {
 };
 
 // Depth of the input pipeline: a warp keeps NST - 1 chunks of input records
-// in flight while it computes on one (the forward pass reads small y
-// records; the reverse passes 64-byte filter records).
+// in flight while it computes on one.  Measured on GB300 (T = 2^20, 2^22):
+// the forward pass (small y records, chunks of up to 4 steps) is fastest
+// with 4 stages, the reverse passes (64-byte filter records, one step per
+// chunk) with 5.
+#ifndef KF_STAGE_NST
+#define KF_STAGE_NST(kind) ((kind) == 0 ? 4 : 5)
+#endif
 template <class P>
-constexpr int stage_nst() { return P::KIND == 0 ? 4 : 3; }
+constexpr int stage_nst() { return KF_STAGE_NST(P::KIND); }
 
 template <int C, int REC, typename R>
 struct WarpStage {
