@@ -110,6 +110,42 @@ def ladner_fischer(a, op):
     return a[1:], n
 
 
+def sengupta(a, op, N=1):
+    """Alg. sengupta (Sengupta et al.): reduce the series into levels
+    a^(d), d = 1 .. d* = log2(T / N), each half as long as the one below
+    (a^(d)_i = a^(d-1)_{2i-1} (x) a^(d-1)_{2i}); run Hillis-Steele (Alg. 1)
+    on a^(d*); then sweep down: a^(d)_i = a^(d+1)_{i/2} for even i and
+    a^(d+1)_{(i-1)/2} (x) a^(d)_i for odd i > 1.  The threshold N must be a
+    power of two (read as such; N > T is taken as N = T).  N = 1 is the
+    paper's "Sengupta A"."""
+    T = len(a)
+    L = _log2(T)
+    N = min(N, T)
+    Ln = _log2(N)
+    dstar = L - Ln
+    lev = [[None] + list(a)]
+    n = 0
+    for d in range(1, dstar + 1):
+        prev, m = lev[d - 1], T >> d
+        cur = [None] * (m + 1)
+        for i in range(1, m + 1):
+            cur[i] = op(prev[2 * i - 1], prev[2 * i])
+            n += 1
+        lev.append(cur)
+    top, nh = hillis_steele(lev[dstar][1:], op)
+    lev[dstar] = [None] + top
+    n += nh
+    for d in range(dstar - 1, -1, -1):
+        up, cur = lev[d + 1], lev[d]
+        for i in range(2, (T >> d) + 1):
+            if i % 2 == 1:
+                cur[i] = op(up[(i - 1) // 2], cur[i])
+                n += 1
+            else:
+                cur[i] = up[i // 2]
+    return lev[0][1:], n
+
+
 def reverse(scan, a, op, *extra):
     """Reversed all-prefix-sums (Sec. II-B) by reversing the series before
     and after the scan, with the operands swapped so that the later element

@@ -367,6 +367,27 @@ def test_scans_on_noncommutative_operator(T):
         assert r == rwant
 
 
+@pytest.mark.parametrize("T", [1, 2, 4, 8, 16, 64, 256])
+@pytest.mark.parametrize("N", [1, 2, 4, 16, 1024])
+def test_sengupta_on_noncommutative_operator(T, N):
+    """Alg. sengupta: exact prefixes of a non-commutative operator, forward
+    and reversed, and its work: 2(T - N) - d* reduce and down-sweep
+    combines plus Hillis-Steele's N log2 N - N + 1 on the top level (so
+    N = 1 does the in-place Ladner-Fischer work 2T - 2 - log2 T)."""
+    a = ["<%d>" % k for k in range(1, T + 1)]
+    want = ["".join(a[:k]) for k in range(1, T + 1)]
+    r, n = scans.sengupta(a, concat, N)
+    assert r == want
+    L = T.bit_length() - 1
+    Ne = min(N, T)
+    Ln = Ne.bit_length() - 1
+    assert n == 2 * (T - Ne) - (L - Ln) + Ne * Ln - Ne + 1
+    if N == 1:
+        assert n == max(2 * T - 2 - L, 0)
+    r, _ = scans.reverse(scans.sengupta, a, concat, N)
+    assert r == ["".join(a[k:]) for k in range(T)]
+
+
 def test_scans_on_kalman_elements():
     model = W.cv_model()
     T = 32
@@ -375,7 +396,9 @@ def test_scans_on_kalman_elements():
     ref, _ = scans.sequential(els, oracle.filter_combine)
     for res, _ in (scans.hillis_steele(els, oracle.filter_combine),
                    scans.blelloch(els, oracle.filter_combine, oracle.FilterElem.identity(4)),
-                   scans.ladner_fischer(els, oracle.filter_combine)):
+                   scans.ladner_fischer(els, oracle.filter_combine),
+                   scans.sengupta(els, oracle.filter_combine, 1),
+                   scans.sengupta(els, oracle.filter_combine, 8)):
         for k in range(T):
             assert rel(res[k].b, ref[k].b) < 1e-10 and rel(res[k].C, ref[k].C) < 1e-10
 
