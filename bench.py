@@ -312,7 +312,10 @@ def workload_sweep(args):
         dt = kf.dtype_of(prec)
         yall = torch.tensor(y64, dtype=dt, device="cuda")
         out[prec] = {}
-        for scan in ("auto", "dlb", "ladner_fischer", "blelloch", "hillis_steele"):
+        for col in ("auto", "dlb", "ladner_fischer", "blelloch", "hillis_steele", "sengupta_a", "sengupta_b"):
+            scan = col[:8] if col.startswith("sengupta") else col
+            # Sengupta A: N = 1; B: N = 16384 (the paper's CUDA runs used 20000)
+            kf.kf_set_option("sengupta_n", 16384 if col == "sengupta_b" else 1)
             row = {}
             for e in range(10, 23):
                 T = 1 << e
@@ -326,7 +329,8 @@ def workload_sweep(args):
                 assert kf.kf_sync_status() == 0
                 row[T] = {"ms": ms_, "steps_per_s": T / (ms_ * 1e-3)}
                 del ws
-            out[prec][scan] = row
+            out[prec][col] = row
+    kf.kf_set_option("sengupta_n", 1)
     if args.save_tuning:   # the entries kf_autotune recorded for every (precision, T) of the sweep
         kf.kf_tuning_save(args.save_tuning)
     print(json.dumps({"workload": "sweep", "metric": "smoothed steps/s", "unit": "smoothed steps/s",

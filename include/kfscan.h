@@ -61,14 +61,18 @@ extern "C" {
 /* Scan algorithm.  DECOUPLED_LOOKBACK is the single-pass scan (one kernel
  * per scan direction, element construction and extraction fused in);
  * HILLIS_STEELE, BLELLOCH and LADNER_FISCHER are Algs. 1, 2 and 3 of Sec. II
- * run level by level over element buffers in device memory (T padded to a
- * power of two with neutral elements).  AUTO picks the decoupled lookback. */
+ * and SENGUPTA is Alg. sengupta (reduce into half-length levels, Hillis-Steele
+ * on the level of length KF_OPT_SENGUPTA_N, down-sweep), run level by level
+ * over element buffers in device memory (T padded to a power of two with
+ * neutral elements).  AUTO takes the autotuner's choice when it has one for
+ * the call, else the decoupled look-back. */
 typedef enum {
     KF_SCAN_AUTO = 0,
     KF_SCAN_DECOUPLED_LOOKBACK = 1,
     KF_SCAN_HILLIS_STEELE = 2,
     KF_SCAN_BLELLOCH = 3,
-    KF_SCAN_LADNER_FISCHER = 4
+    KF_SCAN_LADNER_FISCHER = 4,
+    KF_SCAN_SENGUPTA = 5
 } kf_scan_t;
 
 /* Working precision.  KF_FP32_FP64SOLVE keeps elements, combines and outputs
@@ -270,6 +274,11 @@ kf_status_t kf_sync_status(void *stream);
  *                               aggregates in the look-back: 0 (default: the
  *                               library's choice) or 1 .. 32 (capped at the
  *                               CTA's warp count).
+ *   KF_OPT_SENGUPTA_N           threshold N of KF_SCAN_SENGUPTA: the length
+ *                               of the level scanned by Hillis-Steele, a power
+ *                               of two in 1 .. 2^30 (default 1, the paper's
+ *                               "Sengupta A"; larger N, "Sengupta B", is
+ *                               capped at the padded length).
  * Returns KF_ERR_ARG for an unknown option or a value out of range. */
 typedef enum {
     KF_OPT_WAIT_TIMEOUT_NS = 0,
@@ -277,7 +286,8 @@ typedef enum {
     KF_OPT_POSITIONS_PER_THREAD = 2,
     KF_OPT_THREADS = 3,
     KF_OPT_GENERAL_SOLVE = 4,
-    KF_OPT_LOOKBACK_WARPS = 5
+    KF_OPT_LOOKBACK_WARPS = 5,
+    KF_OPT_SENGUPTA_N = 6
 } kf_option_t;
 kf_status_t kf_set_option(kf_option_t opt, int64_t value);
 int64_t kf_get_option(kf_option_t opt); /* -1 for an unknown option */

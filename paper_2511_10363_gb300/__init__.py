@@ -24,13 +24,13 @@ LIB_PATH = _build.LIB
 
 # enums of kfscan.h
 SCANS = {"auto": 0, "dlb": 1, "decoupled_lookback": 1, "hillis_steele": 2, "hs": 2,
-         "blelloch": 3, "ladner_fischer": 4, "lafi": 4}
+         "blelloch": 3, "ladner_fischer": 4, "lafi": 4, "sengupta": 5}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_fp64solve": 2, "mixed": 2}
 OPS = {"filter": 0, "rts": 1, "two_filter": 2, "tf": 2}
 STATUS = {0: "KF_OK", 1: "KF_ERR_ARG", 2: "KF_ERR_NOT_PD", 3: "KF_ERR_CUDA", 4: "KF_ERR_OOM",
           5: "KF_ERR_TIMEOUT", 6: "KF_ERR_BUDGET", 7: "KF_ERR_BUSY", 8: "KF_ERR_CAPACITY"}
 OPTIONS = {"wait_timeout_ns": 0, "test_skip_tile": 1, "positions_per_thread": 2, "threads": 3, "general_solve": 4,
-           "lookback_warps": 5}
+           "lookback_warps": 5, "sengupta_n": 6}
 
 _lib = None
 
@@ -438,7 +438,7 @@ class Server:
             pass
 
 
-SCAN_NAMES = {1: "dlb", 2: "hillis_steele", 3: "blelloch", 4: "ladner_fischer"}
+SCAN_NAMES = {1: "dlb", 2: "hillis_steele", 3: "blelloch", 4: "ladner_fischer", 5: "sengupta"}
 
 
 def kf_autotune(op, model, y, precision="fp32", reps=5, workspace=None, stream=None):

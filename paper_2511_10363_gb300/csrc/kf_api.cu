@@ -232,7 +232,7 @@ static std::mutex g_mu;
 static void *g_ws[64];
 static size_t g_ws_bytes[64];
 static int *g_status[64];
-static std::atomic<int64_t> g_opt[8] = {1000000000LL, -1, 0, 0, 0, 0, 0, 0};
+static std::atomic<int64_t> g_opt[8] = {1000000000LL, -1, 0, 0, 0, 0, 1, 0};
 
 // KFSCAN_DEBUG=1 in the environment logs each stage of a call to stderr.
 bool debug_on() {
@@ -512,7 +512,7 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
     if (s != KF_OK) return s;
     if (T < 1 || T > (int64_t(1) << 40) || !y) return KF_ERR_ARG;
     if (prec != KF_FP64 && prec != KF_FP32 && prec != KF_FP32_FP64SOLVE) return KF_ERR_ARG;
-    if (scan < KF_SCAN_AUTO || scan > KF_SCAN_LADNER_FISCHER) return KF_ERR_ARG;
+    if (scan < KF_SCAN_AUTO || scan > KF_SCAN_SENGUPTA) return KF_ERR_ARG;
     const size_t w = (prec == KF_FP64) ? 8 : 4;
     LaunchReq q;
     memset(&q, 0, sizeof(q));
@@ -552,6 +552,7 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
     q.threads = int(g_opt[KF_OPT_THREADS].load());
     q.no_lowrank = int(g_opt[KF_OPT_GENERAL_SOLVE].load());
     q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
+    q.sg_n = g_opt[KF_OPT_SENGUPTA_N].load();
     TuneCfg tc;
     if (scan == KF_SCAN_AUTO && tuned(op, md->nx, md->ny, q.prec, T, &tc)) {
         q.scan = tc.scan;
@@ -802,7 +803,7 @@ size_t kf_workspace_size(kf_op_t op, int nx, int ny, int64_t total_steps, kf_pre
     if ((nx != 2 && nx != 4 && nx != 8) || ny < 1 || ny > KF_MAXM || total_steps < 1) return 0;
     if (op < KF_OP_FILTER || op > KF_OP_TWO_FILTER) return 0;
     if (prec != KF_FP64 && prec != KF_FP32 && prec != KF_FP32_FP64SOLVE) return 0;
-    if (scan < KF_SCAN_AUTO || scan > KF_SCAN_LADNER_FISCHER) return 0;
+    if (scan < KF_SCAN_AUTO || scan > KF_SCAN_SENGUPTA) return 0;
     if (scan == KF_SCAN_AUTO) {   // room for whichever algorithm the tuning table may pick
         const size_t a = ws_bytes_dispatch(nx, int(op), int(prec), KF_SCAN_DLB_I, total_steps);
         const size_t b = ws_bytes_dispatch(nx, int(op), int(prec), KF_SCAN_LAFI_I, total_steps);
@@ -1113,8 +1114,10 @@ kf_status_t kf_measure_fma_peak(int fp64, double *flops_per_second) {
 }
 
 kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_LOOKBACK_WARPS) return KF_ERR_ARG;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_SENGUPTA_N) return KF_ERR_ARG;
     if (opt == KF_OPT_GENERAL_SOLVE && value != 0 && value != 1) return KF_ERR_ARG;
+    if (opt == KF_OPT_SENGUPTA_N && (value < 1 || value > (int64_t(1) << 30) || (value & (value - 1)) != 0))
+        return KF_ERR_ARG;
     if (opt == KF_OPT_LOOKBACK_WARPS && (value < 0 || value > 32)) return KF_ERR_ARG;
     if (opt == KF_OPT_WAIT_TIMEOUT_NS && (value < 1000000 || value > 60000000000LL)) return KF_ERR_ARG;
     if (opt == KF_OPT_POSITIONS_PER_THREAD && (value < 0 || value > (1 << 24))) return KF_ERR_ARG;
@@ -1124,7 +1127,7 @@ kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
 }
 
 int64_t kf_get_option(kf_option_t opt) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_LOOKBACK_WARPS) return -1;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_SENGUPTA_N) return -1;
     return g_opt[opt].load();
 }
 

@@ -19,6 +19,7 @@
 #define KF_SCAN_HS_I 2
 #define KF_SCAN_BLELLOCH_I 3
 #define KF_SCAN_LAFI_I 4
+#define KF_SCAN_SG_I 5
 #define KF_FP64_I 0
 #define KF_FP32_I 1
 #define KF_FP32_FP64SOLVE_I 2
@@ -56,6 +57,7 @@ struct LaunchReq {
     int lookback_warps;  // warps of a CTA that take part in the look-back (0: all)
     double *ll_step;     // per-step log-likelihood terms (batched calls; set by the batch launcher)
     int no_alloc;        // the call may not allocate: no device table cache
+    int64_t sg_n;        // Sengupta threshold N (power of two)
 };
 
 // Device cache of tile-scan tables (kf_api.cu): a table is found by its key,

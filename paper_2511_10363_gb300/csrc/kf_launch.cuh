@@ -401,7 +401,12 @@ WsLayout ws_layout(int op, int scan, int64_t T) {
     if (scan != KF_SCAN_DLB_I) {
         const int64_t Tp = next_pow2(T);
         L.lv_a = o; o += al256(size_t(Tp) * ES * sizeof(R));
-        if (scan == KF_SCAN_HS_I || scan == KF_SCAN_BLELLOCH_I) { L.lv_b = o; o += al256(size_t(Tp) * ES * sizeof(R)); }
+        // second buffer: HS and Blelloch double-buffer; Sengupta keeps its
+        // levels 1..d* (Tpad - N elements) and a Hillis-Steele scratch of N
+        if (scan == KF_SCAN_HS_I || scan == KF_SCAN_BLELLOCH_I || scan == KF_SCAN_SG_I) {
+            L.lv_b = o;
+            o += al256(size_t(Tp) * ES * sizeof(R));
+        }
     }
     L.total = o;
     return L;
@@ -615,6 +620,43 @@ static cudaError_t run_levels(const typename P::Args &args, char *ws, size_t ctl
         lv_set_identity<P><<<1, 32, 0, st>>>(a, Tp, Tp - 1);
         for (int d = Lg - 1; d >= 0; --d) lv_blelloch_down<P><<<lv_grid(Tp >> (d + 1), LT), LT, 0, st>>>(a, Tp, d);
         lv_blelloch_final<P><<<lv_grid(Tp, LT), LT, 0, st>>>(a, b, Tp);
+    } else if (q.scan == KF_SCAN_SG_I) {
+        // Alg. sengupta: levels a^(d), d = 1..d*, of length Tp / 2^d packed
+        // one after another in b (structure of arrays, stride = the level's
+        // length), Hillis-Steele on a^(d*) of length N, down-sweep into a
+        const int64_t N = q.sg_n < Tp ? q.sg_n : Tp;
+        int Ln = 0;
+        while ((int64_t(1) << Ln) < N) ++Ln;
+        const int dstar = Lg - Ln;
+        R *lev[64];
+        int64_t len[64];
+        lev[0] = a;
+        len[0] = Tp;
+        int64_t off = 0;
+        for (int d = 1; d <= dstar; ++d) {
+            len[d] = Tp >> d;
+            lev[d] = b + off;
+            off += int64_t(P::Elem::SIZE) * len[d];
+        }
+        R *scratch = (dstar == 0) ? b : b + off;   // room for one level of length N
+        nl = 1;
+        lv_build<P><<<lv_grid(Tp, LT), LT, 0, st>>>(args, a, nullptr, Tp);
+        for (int d = 1; d <= dstar; ++d) {
+            lv_sg_reduce<P><<<lv_grid(len[d], LT), LT, 0, st>>>(lev[d - 1], len[d - 1], lev[d], len[d]);
+            ++nl;
+        }
+        R *src = lev[dstar], *dst = scratch;
+        for (int e = 0; e < Ln; ++e) {
+            lv_hillis_steele<P><<<lv_grid(len[dstar], LT), LT, 0, st>>>(src, dst, len[dstar], int64_t(1) << e);
+            R *t = src; src = dst; dst = t;
+            ++nl;
+        }
+        lev[dstar] = src;   // the scanned top level (in place or in the scratch)
+        for (int d = dstar - 1; d >= 0; --d) {
+            lv_sg_down<P><<<lv_grid(len[d], LT), LT, 0, st>>>(lev[d + 1], len[d + 1], lev[d], len[d]);
+            ++nl;
+        }
+        res = lev[0];
     } else {  // Ladner-Fischer
         nl = 1 + Lg;
         lv_build<P><<<lv_grid(Tp, LT), LT, 0, st>>>(args, a, nullptr, Tp);

@@ -1,7 +1,7 @@
 // scan_levels.cuh -- the all-prefix-sum algorithms of Sec. II of
 // arXiv 2511.10363 run level by level over element buffers in device memory:
-// Hillis-Steele (Alg. 1), Blelloch (Alg. 2) and the in-place Ladner-Fischer
-// circuit (Alg. 3).  One launch per level; each launch covers the level's
+// Hillis-Steele (Alg. 1), Blelloch (Alg. 2), the in-place Ladner-Fischer
+// circuit (Alg. 3) and the hybrid of Sengupta et al. (Alg. sengupta).  One launch per level; each launch covers the level's
 // independent operator applications with a grid-stride loop.
 //
 // Elements are stored structure-of-arrays by scalar component,
@@ -63,6 +63,41 @@ __global__ void lv_hillis_steele(const typename P::R *src, typename P::R *dst, i
             store_soa(o, dst, Tpad, j);
         } else {
             store_soa(y, dst, Tpad, j);
+        }
+    }
+}
+
+// Alg. sengupta, reduce pass: dst_i = src_{2i-1} (x) src_{2i} (1-based),
+// src of length ls, dst of length ld = ls / 2 (each its own stride).
+template <class P>
+__global__ void lv_sg_reduce(const typename P::R *src, int64_t ls, typename P::R *dst, int64_t ld) {
+    using Elem = typename P::Elem;
+    for (int64_t i = gtid(); i < ld; i += gstride()) {
+        Elem x, y, o;
+        load_soa(x, src, ls, 2 * i);
+        load_soa(y, src, ls, 2 * i + 1);
+        P::combine(x, y, o);
+        store_soa(o, dst, ld, i);
+    }
+}
+
+// Alg. sengupta, down-sweep of one level: with `up` the scanned level above,
+// cur_i = up_{i/2} for even i and up_{(i-1)/2} (x) cur_i for odd i > 1
+// (1-based; cur_1 stays).
+template <class P>
+__global__ void lv_sg_down(const typename P::R *up, int64_t lu, typename P::R *cur, int64_t lc) {
+    using Elem = typename P::Elem;
+    for (int64_t i = gtid() + 1; i < lc; i += gstride()) {   // 0-based; index 0 stays
+        Elem x;
+        if (i & 1) {          // 1-based i + 1 even
+            load_soa(x, up, lu, (i - 1) / 2);
+            store_soa(x, cur, lc, i);
+        } else {              // 1-based i + 1 odd, > 1
+            Elem y, o;
+            load_soa(x, up, lu, i / 2 - 1);
+            load_soa(y, cur, lc, i);
+            P::combine(x, y, o);
+            store_soa(o, cur, lc, i);
         }
     }
 }

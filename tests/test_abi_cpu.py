@@ -99,6 +99,19 @@ def test_workspace_size(lib):
     assert kf.kf_workspace_size("rts", 4, 9, 100) == 0
 
 
+def test_sengupta_option(lib):
+    assert kf.kf_get_option("sengupta_n") == 1
+    for bad in (0, 3, 12, 1 << 31):
+        with pytest.raises(kf.KfError):
+            kf.kf_set_option("sengupta_n", bad)
+    kf.kf_set_option("sengupta_n", 16384)
+    assert kf.kf_get_option("sengupta_n") == 16384
+    kf.kf_set_option("sengupta_n", 1)
+    # levels and Hillis-Steele scratch fit in the second level buffer
+    assert kf.kf_workspace_size("rts", 4, 2, 1000, "fp32", "sengupta") == \
+        kf.kf_workspace_size("rts", 4, 2, 1000, "fp32", "blelloch")
+
+
 def test_options(lib):
     assert kf.kf_get_option("wait_timeout_ns") == 10 ** 9
     with pytest.raises(kf.KfError):

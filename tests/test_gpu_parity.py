@@ -13,7 +13,7 @@ from tests.gpu_util import TOL, gpu_run, oracle_inputs, oracle_run, mean_err, co
 
 pytestmark = pytest.mark.gpu
 
-SCANS = ["dlb", "hillis_steele", "blelloch", "ladner_fischer"]
+SCANS = ["dlb", "hillis_steele", "blelloch", "ladner_fischer", "sengupta"]
 PRECS = ["fp64", "fp32", "fp32_fp64solve"]
 
 
@@ -73,6 +73,23 @@ def test_level_scan_parity(op, scan, precision, T):
     model = W.cv_model()
     y = W.simulate(model, T, seed=2000 + T)
     compare(op, model, y, precision, scan)
+
+
+@pytest.mark.parametrize("N", [2, 16, 1 << 20])
+@pytest.mark.parametrize("T", [5, 64, 333])
+def test_sengupta_threshold(N, T):
+    """Alg. sengupta with a Hillis-Steele top level of length N ("Sengupta
+    B"; N beyond the padded length makes it Hillis-Steele outright)."""
+    import paper_2511_10363_gb300 as kf
+    model = W.cv_model()
+    y = W.simulate(model, T, seed=900 + T)
+    kf.kf_set_option("sengupta_n", N)
+    try:
+        for op in ("filter", "rts", "tf"):
+            compare(op, model, y, "fp64", "sengupta")
+        compare("rts", model, y, "fp32", "sengupta")
+    finally:
+        kf.kf_set_option("sengupta_n", 1)
 
 
 @pytest.mark.parametrize("K", [1, 2, 3, 7])
