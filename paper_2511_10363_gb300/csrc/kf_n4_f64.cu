@@ -11,6 +11,5 @@ size_t batch_ws_bytes_n4_f64(int op, int64_t T, int nseq, int nmodels, int logli
     return batch_layout<4, double>(op, T, nseq, nmodels, loglik != 0).total;
 }
 
-cudaError_t launch_batch_n4_f64(const LaunchReq &q, const BatchReq &b) { return launch_batch_typed<4, double, 0, 128>(q, b); }
 
 }  // namespace kfs
