@@ -220,8 +220,11 @@ struct FoldTab {
     static constexpr int S = N * (N + 1) / 2;
     static constexpr int E = N * N + 2 * N * M;                       // row: T1 | T4 | T3U
     static constexpr int E1 = N * N + N * M;                          // first-run row: T1' | T4'
-    static constexpr int KT0 = 8192 / (E * int(sizeof(R)));
-    static constexpr int KT = KT0 < 64 ? KT0 : 64;                    // rows (<= 8 KB)
+    // rows: up to 16 KB (FP32) / 12 KB (FP64) of T1 | T4 | T3U, at most 128;
+    // with the first-run rows and the model constants the kernel parameters
+    // stay within their 32 KB
+    static constexpr int KT0 = (sizeof(R) == 4 ? 16384 : 12288) / (E * int(sizeof(R)));
+    static constexpr int KT = KT0 < 128 ? KT0 : 128;
     int K;                                                            // 0: no table
     R A[N * N], C[S], J[S];                                           // aggregate of K fresh elements
     R C1K[S];                                                         // P_{K|K}: C of the first run

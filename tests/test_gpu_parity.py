@@ -151,13 +151,13 @@ def test_filter_solve_forms(general, precision, nx):
 
 
 @pytest.mark.parametrize("threads", [128, 256])
-@pytest.mark.parametrize("K", [2, 3, 16, 33, 34, 65, 66, 200])
+@pytest.mark.parametrize("K", [2, 3, 16, 49, 50, 129, 130, 200])
 @pytest.mark.parametrize("model_kind", ["cv", "random4", "random2"])
 def test_fold_table(K, model_kind, threads):
     """With ny = nx / 2 and one sequence, the thread fold of the filter scan
     reads the (A, C, J) half of its aggregate from a table built per launch
-    for K positions per thread (up to 65 rows in FP32, 33 in FP64; beyond
-    that the per-step solve is used); the tiles whose threads all use the
+    for K positions per thread (K up to 129 in FP32 for nx = 4, 49 in FP64;
+    beyond that the per-step solve is used); the tiles whose threads all use the
     fold table also run their tile scan on (b, eta) with the tile-scan
     table.  Forced K across the table limits, a ragged last thread, many
     tiles, 128- and 256-thread CTAs (256 exists for nx = 4 in FP32)."""
