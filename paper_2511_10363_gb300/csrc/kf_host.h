@@ -58,6 +58,7 @@ struct LaunchReq {
     double *ll_step;     // per-step log-likelihood terms (batched calls; set by the batch launcher)
     int no_alloc;        // the call may not allocate: no device table cache
     int64_t sg_n;        // Sengupta threshold N (power of two)
+    int counters_zeroed; // the look-back counters of this pass were cleared already
 };
 
 // Device cache of tile-scan tables (kf_api.cu): a table is found by its key,

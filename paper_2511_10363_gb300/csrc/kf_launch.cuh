@@ -5,6 +5,7 @@
 #include "kf_host.h"
 #include <math.h>
 #include <mutex>
+#include <new>
 #include <stdio.h>
 
 #include "scan_levels.cuh"
@@ -194,6 +195,61 @@ static void build_fold_table(const HostModel &h, int K, FoldTab<N, M, R> &t, dou
 }
 static inline void build_fold_table(const HostModel &, int, NoTab &t, double * = nullptr) { t.K = 0; }
 
+// FNV-1a over bytes
+static inline uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
+
+// build_fold_table behind a small host cache keyed by the model constants it
+// reads and K (a repeated call on the same model skips the K-step FP64
+// recursion).
+template <int N, int M, typename R>
+static void cached_fold_table(const HostModel &h, int K, FoldTab<N, M, R> &t, double *agg64) {
+    struct Entry {
+        uint64_t key;
+        FoldTab<N, M, R> tab;
+        double agg[3 * N * N];
+    };
+    static std::mutex mu;
+    static Entry *cache = nullptr;   // 8 entries, replaced round robin
+    static int nfill = 0, next = 0;
+    constexpr int NN = N * N, NM = N * M;
+    uint64_t key = fnv1a(&K, sizeof(K));
+    key = fnv1a(&h.n, sizeof(h.n), key);
+    key = fnv1a(&h.m, sizeof(h.m), key);
+    key = fnv1a(h.A, sizeof(double) * NN, key);
+    key = fnv1a(h.C, sizeof(double) * NN, key);
+    key = fnv1a(h.J, sizeof(double) * NN, key);
+    key = fnv1a(h.C1, sizeof(double) * NN, key);
+    key = fnv1a(h.K, sizeof(double) * NM, key);
+    key = fnv1a(h.G, sizeof(double) * NM, key);
+    key = fnv1a(h.U, sizeof(double) * NM, key);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (int i = 0; i < nfill; ++i)
+            if (cache[i].key == key) {
+                t = cache[i].tab;
+                for (int j = 0; j < 3 * NN; ++j) agg64[j] = cache[i].agg[j];
+                return;
+            }
+    }
+    build_fold_table(h, K, t, agg64);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cache) cache = new (std::nothrow) Entry[8];
+    if (!cache) return;
+    Entry &e = cache[next];
+    next = (next + 1) % 8;
+    if (nfill < 8) ++nfill;
+    e.key = key;
+    e.tab = t;
+    for (int j = 0; j < 3 * NN; ++j) e.agg[j] = agg64[j];
+}
+static inline void cached_fold_table(const HostModel &h, int K, NoTab &t, double *agg64) {
+    build_fold_table(h, K, t, agg64);
+}
+
 // (A, C, J) half of Lemma 1 for x (x) y, full N x N matrices in FP64.
 template <int N>
 static bool host_acj_combine(const double *x, const double *y, double *o) {
@@ -288,12 +344,7 @@ static bool build_scan_table(const double *chunk, int nw, R *out) {
     return true;
 }
 
-// FNV-1a over bytes
-static inline uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
-    const unsigned char *c = static_cast<const unsigned char *>(p);
-    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
-    return h;
-}
+
 
 // ---------------------------------------------------------------- tile plan
 
@@ -525,7 +576,7 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
     if constexpr (P::TABLE) {
         using ST = ScanTab<P::NX, typename P::R>;
         double chunk[3 * P::NX * P::NX] = {};
-        build_fold_table(*q.hm, tp.K, a2.tab, chunk);
+        cached_fold_table(*q.hm, tp.K, a2.tab, chunk);
         if (a2.tab.K == 0) ctl.sm_tab = -1;
         // tile-scan table: cached on the device by its key (the fold table
         // and the CTA size determine it)
@@ -558,7 +609,8 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
     ctl.trace = nullptr;
     ctl.trace_cap = 0;
     trace_target(P::KIND, &ctl.trace, &ctl.trace_cap);
-    cudaError_t e = cudaMemsetAsync(ctl.counters, 0, sizeof(int) * (2 + tp.ntiles), q.stream);
+    cudaError_t e = q.counters_zeroed ? cudaSuccess
+                                      : cudaMemsetAsync(ctl.counters, 0, sizeof(int) * (2 + tp.ntiles), q.stream);
     if (debug_on())
         fprintf(stderr, "[kfscan] dlb: total=%lld tiles=%d K=%d C=%d threads=%d smem=%d memset=%d\n",
                 (long long)total, tp.ntiles, tp.K, C, THREADS, smem, int(e));
@@ -739,20 +791,26 @@ static cudaError_t launch_typed(const LaunchReq &q) {
     fa.want_ll = q.loglik != nullptr;
     // low-rank filter path when ny = nx / 2
     const bool lowrank = q.hm->m == N / 2 && q.scan == KF_SCAN_DLB_I && !q.no_lowrank;
-    cudaError_t e = filter_pass<N, R, MODE, Src, THREADS, V, false>(fa, lowrank, ws, L, q, q.loglik);
+    LaunchReq qz = q;   // two look-back passes: one memset clears both passes' counters
+    if (q.scan == KF_SCAN_DLB_I && q.op != KF_OP_FILTER_I) {
+        const cudaError_t ez = cudaMemsetAsync(ws + L.ctl_f, 0, L.agg - L.ctl_f, q.stream);
+        if (ez != cudaSuccess) return ez;
+        qz.counters_zeroed = 1;
+    }
+    cudaError_t e = filter_pass<N, R, MODE, Src, THREADS, V, false>(fa, lowrank, ws, L, qz, q.loglik);
     if (e != cudaSuccess || q.op == KF_OP_FILTER_I) return e;
     if (q.op == KF_OP_RTS_I) {
         typename RtsRev<N, R, Src>::Args ra;
         ra.src = fa.src;
         ra.buf = buf;
         ra.want_ll = 0;
-        return run_scan<RtsRev<N, R, Src>, THREADS, V>(ra, ws, L.ctl_r, L, q, nullptr);
+        return run_scan<RtsRev<N, R, Src>, THREADS, V>(ra, ws, L.ctl_r, L, qz, nullptr);
     }
     typename TfRev<N, R, MODE, Src>::Args ta;
     ta.src = fa.src;
     ta.buf = buf;
     ta.want_ll = 0;
-    return run_scan<TfRev<N, R, MODE, Src>, THREADS, V>(ta, ws, L.ctl_r, L, q, nullptr);
+    return run_scan<TfRev<N, R, MODE, Src>, THREADS, V>(ta, ws, L.ctl_r, L, qz, nullptr);
 }
 
 template <int N>
