@@ -52,6 +52,11 @@ def _load():
         lib.orc_rts_element.argtypes = [i, D, D, i, D, D, D]
         lib.orc_rts_combine.argtypes = [i, D, D, D]
         lib.orc_rts_combine.restype = None
+        lib.orc_tv_kf.argtypes = [i, i, D, D, D, D, D, D, D, D, l, D, D, D, D]
+        lib.orc_tv_rts.argtypes = [i, D, D, D, l, D, D, D, D]
+        lib.orc_tv_tf.argtypes = [i, i, D, D, D, D, D, D, l, D, D, D, D, D, D, D]
+        lib.orc_tv_filter_element.argtypes = [i, i, D, D, D, D, D, D, D, D, i, D, D]
+        lib.orc_tv_rts_element.argtypes = [i, D, D, D, i, D, D, D]
         _lib = lib
     return _lib
 
@@ -225,4 +230,103 @@ def rts_combine(ei: RtsElem, ej: RtsElem) -> RtsElem:
     a, b = _c(ei.flat()), _c(ej.flat())
     out = np.empty_like(a)
     _load().orc_rts_combine(n, _p(a), _p(b), _p(out))
+    return RtsElem.unflat(out, n)
+
+
+# ---- time-varying model (Sec. III-A with per-step F, Q, u, H, R, d) -------
+#
+# A time-varying model is a dict of per-step arrays: record t = 0 .. T-1
+# belongs to time k = t + 1 and holds F[t] = F_{k-1}, Q[t] = Q_{k-1},
+# u[t] = u_{k-1} (or u = None), H[t] = H_k, R[t] = R_k, d[t] = d_k (or
+# d = None); m0, P0 are the prior xbar_{0|0}, P_{0|0}.
+
+def _tv(model):
+    F, Q, H, R = (_c(model[k]) for k in ("F", "Q", "H", "R"))
+    u = None if model.get("u") is None else _c(model["u"])
+    d = None if model.get("d") is None else _c(model["d"])
+    return F, Q, u, H, R, d, _c(model["m0"]), _c(model["P0"])
+
+
+def tv_kf(model, y):
+    """Sequential Kalman filter for a time-varying model: (m, P, loglik)."""
+    F, Q, u, H, R, d, m0, P0 = _tv(model)
+    y = _c(y)
+    T, ny = y.shape
+    nx = F.shape[1]
+    m = np.empty((T, nx))
+    P = np.empty((T, nx, nx))
+    ll = np.zeros(1)
+    if _load().orc_tv_kf(nx, ny, _p(F), _p(Q), _p(u), _p(H), _p(R), _p(d), _p(m0), _p(P0), T, _p(y), _p(m),
+                         _p(P), _p(ll)):
+        raise ArithmeticError("oracle TV KF: innovation covariance not positive definite")
+    return m, P, float(ll[0])
+
+
+def tv_rts(model, mf, Pf):
+    """Sequential RTS smoother for a time-varying model."""
+    F, Q, u, _, _, _, _, _ = _tv(model)
+    mf, Pf = _c(mf), _c(Pf)
+    T, nx = mf.shape
+    ms = np.empty_like(mf)
+    Ps = np.empty_like(Pf)
+    if _load().orc_tv_rts(nx, _p(F), _p(Q), _p(u), T, _p(mf), _p(Pf), _p(ms), _p(Ps)):
+        raise ArithmeticError("oracle TV RTS: singular predicted covariance")
+    return ms, Ps
+
+
+def tv_tf(model, y, mf, Pf, want_info=False):
+    """Sequential two-filter smoother for a time-varying model."""
+    F, Q, u, H, R, d, _, _ = _tv(model)
+    y, mf, Pf = _c(y), _c(mf), _c(Pf)
+    T, ny = y.shape
+    nx = F.shape[1]
+    ms = np.empty_like(mf)
+    Ps = np.empty_like(Pf)
+    eta = np.empty((T, nx)) if want_info else None
+    J = np.empty((T, nx, nx)) if want_info else None
+    if _load().orc_tv_tf(nx, ny, _p(F), _p(Q), _p(u), _p(H), _p(R), _p(d), T, _p(y), _p(mf), _p(Pf), _p(ms),
+                         _p(Ps), _p(eta), _p(J)):
+        raise ArithmeticError("oracle TV TF: singular system")
+    if want_info:
+        return ms, Ps, eta, J
+    return ms, Ps
+
+
+def tv_smooth(model, y, kind="rts"):
+    """Filter then smooth a time-varying model: (ms, Ps, mf, Pf, loglik)."""
+    mf, Pf, ll = tv_kf(model, y)
+    if kind == "rts":
+        ms, Ps = tv_rts(model, mf, Pf)
+    elif kind == "tf":
+        ms, Ps = tv_tf(model, y, mf, Pf)
+    else:
+        raise ValueError(kind)
+    return ms, Ps, mf, Pf, ll
+
+
+def tv_filter_element(model, k, yk):
+    """Element a_k (k 1-based) of Eqs. pkf_init1/2/3 with the step's
+    F_{k-1}, Q_{k-1}, u_{k-1}, H_k, R_k, d_k."""
+    F, Q, u, H, R, d, m0, P0 = _tv(model)
+    t = int(k) - 1
+    nx, ny = F.shape[1], H.shape[1]
+    out = np.empty(3 * nx * nx + 2 * nx)
+    ut = None if u is None else _c(u[t])
+    dt = None if d is None else _c(d[t])
+    if _load().orc_tv_filter_element(nx, ny, _p(_c(F[t])), _p(_c(Q[t])), _p(ut), _p(_c(H[t])), _p(_c(R[t])),
+                                     _p(dt), _p(m0), _p(P0), int(k == 1), _p(_c(yk)), _p(out)):
+        raise ArithmeticError("oracle TV element: S not positive definite")
+    return FilterElem.unflat(out, nx)
+
+
+def tv_rts_element(model, k, T, xk, Pk):
+    """Element of Eqs. prts_init1 (k < T, with F_k, Q_k, u_k) / prts_init2 (k = T)."""
+    F, Q, u, _, _, _, _, _ = _tv(model)
+    n = F.shape[1]
+    out = np.empty(2 * n * n + n)
+    last = int(k == T)
+    t = min(int(k), F.shape[0] - 1)          # record k holds F_k, Q_k, u_k (unused at k = T)
+    ut = None if u is None else _c(u[t])
+    if _load().orc_tv_rts_element(n, _p(_c(F[t])), _p(_c(Q[t])), _p(ut), last, _p(_c(xk)), _p(_c(Pk)), _p(out)):
+        raise ArithmeticError("oracle TV RTS element: singular predicted covariance")
     return RtsElem.unflat(out, n)

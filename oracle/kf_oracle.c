@@ -477,3 +477,276 @@ void orc_rts_combine(int n, const double *ei, const double *ej, double *out) {
     memcpy(out + n * n, rg, sizeof(double) * n);
     memcpy(out + n * n + n, rL, sizeof(double) * n * n);
 }
+
+/* ------------------------------------------------------------------ */
+/* Time-varying model (Sec. III-A, the transition and measurement      */
+/* densities with per-step F_{k-1}, Q_{k-1}, u_{k-1}, H_k, R_k, d_k)    */
+/* ------------------------------------------------------------------ */
+/* Step record t = 0 .. T-1 belongs to time k = t + 1 and holds
+ *     F[t] = F_{k-1}, Q[t] = Q_{k-1}, u[t] = u_{k-1}   (n x n, n x n, n)
+ *     H[t] = H_k,     R[t] = R_k,     d[t] = d_k       (m x n, m x m, m)
+ * and y[t] = y_k.  u and d may be NULL (zero).  The smoothers use
+ * F_k, Q_k, u_k of the step into time k + 1, i.e. record k. */
+
+static void vec_or_zero(int len, const double *base, long t, double *out) {
+    if (base) memcpy(out, base + t * len, sizeof(double) * len);
+    else memset(out, 0, sizeof(double) * len);
+}
+
+/* Sequential Kalman filter, Eqs. KF_mean_pred .. KF_cov_upd, with the
+ * innovation log-likelihood sum_k -1/2 (v^T S_k^{-1} v + log det S_k + m log 2 pi),
+ * v = y_k - H_k xbar_{k|k-1} - d_k. */
+int orc_tv_kf(int n, int m, const double *F, const double *Q, const double *u, const double *H, const double *R,
+              const double *d, const double *m0, const double *P0, long T, const double *y,
+              double *m_out, double *P_out, double *loglik) {
+    double x[ORC_MAXN], P[ORC_MAXN * ORC_MAXN], xp[ORC_MAXN], Pp[ORC_MAXN * ORC_MAXN];
+    double t1[ORC_MAXN * ORC_MAXN], t2[ORC_MAXN * ORC_MAXN], Ft[ORC_MAXN * ORC_MAXN], Ht[ORC_MAXN * ORC_MAXN];
+    double S[ORC_MAXN * ORC_MAXN], PHt[ORC_MAXN * ORC_MAXN], KT[ORC_MAXN * ORC_MAXN];
+    double v[ORC_MAXN], Siv[ORC_MAXN], uk[ORC_MAXN], dk[ORC_MAXN];
+    double ll = 0.0;
+    const double LOG2PI = 1.8378770664093454835606594728112;
+    memcpy(x, m0, sizeof(double) * n);
+    memcpy(P, P0, sizeof(double) * n * n);
+    for (long t = 0; t < T; ++t) {
+        const double *Fk = F + t * n * n, *Qk = Q + t * n * n, *Hk = H + t * m * n, *Rk = R + t * m * m;
+        vec_or_zero(n, u, t, uk);
+        vec_or_zero(m, d, t, dk);
+        /* prediction: xbar_{k|k-1} = F_{k-1} xbar + u_{k-1}, P_{k|k-1} = F P F^T + Q_{k-1} */
+        tr(n, n, Fk, Ft);
+        mm(n, n, 1, Fk, x, xp);
+        add(n, xp, uk, xp);
+        mm(n, n, n, Fk, P, t1);
+        mm(n, n, n, t1, Ft, t2);
+        add(n * n, t2, Qk, Pp);
+        /* update: S_k = H_k P_{k|k-1} H_k^T + R_k */
+        tr(m, n, Hk, Ht);
+        mm(n, n, m, Pp, Ht, PHt);
+        mm(m, n, m, Hk, PHt, t1);
+        add(m * m, t1, Rk, S);
+        /* v = y_k - H_k xbar_{k|k-1} - d_k */
+        mm(m, n, 1, Hk, xp, t1);
+        sub(m, y + t * m, t1, v);
+        sub(m, v, dk, v);
+        tr(n, m, PHt, t1);
+        double logdetS;
+        if (chol_solve(m, n, S, t1, KT, &logdetS)) return -1;
+        if (chol_solve(m, 1, S, v, Siv, NULL)) return -1;
+        mm(n, m, 1, PHt, Siv, t2);
+        add(n, xp, t2, x);                           /* xbar_{k|k} */
+        mm(n, m, n, PHt, KT, t2);
+        sub(n * n, Pp, t2, P);                       /* P_{k|k} */
+        memcpy(m_out + t * n, x, sizeof(double) * n);
+        memcpy(P_out + t * n * n, P, sizeof(double) * n * n);
+        double q = 0.0;
+        for (int i = 0; i < m; ++i) q += v[i] * Siv[i];
+        ll += -0.5 * (q + logdetS + m * LOG2PI);
+    }
+    if (loglik) *loglik = ll;
+    return 0;
+}
+
+/* Sequential RTS smoother for k = T-1 .. 1 with the step k -> k+1:
+ * xbar_{k+1|k} = F_k xbar_{k|k} + u_k, P_{k+1|k} = F_k P_{k|k} F_k^T + Q_k,
+ * G_k = P_{k|k} F_k^T P_{k+1|k}^{-1}, then the Sec. III-B recursion. */
+int orc_tv_rts(int n, const double *F, const double *Q, const double *u, long T, const double *mf, const double *Pf,
+               double *ms, double *Ps) {
+    double Ft[ORC_MAXN * ORC_MAXN], Pp[ORC_MAXN * ORC_MAXN], xp[ORC_MAXN], uk[ORC_MAXN];
+    double t1[ORC_MAXN * ORC_MAXN], t2[ORC_MAXN * ORC_MAXN], G[ORC_MAXN * ORC_MAXN], Gt[ORC_MAXN * ORC_MAXN];
+    double dx[ORC_MAXN], dP[ORC_MAXN * ORC_MAXN];
+    memcpy(ms + (T - 1) * n, mf + (T - 1) * n, sizeof(double) * n);
+    memcpy(Ps + (T - 1) * n * n, Pf + (T - 1) * n * n, sizeof(double) * n * n);
+    for (long t = T - 2; t >= 0; --t) {             /* time k = t + 1, step record k = t + 1 */
+        const double *x = mf + t * n, *P = Pf + t * n * n;
+        const double *Fk = F + (t + 1) * n * n, *Qk = Q + (t + 1) * n * n;
+        vec_or_zero(n, u, t + 1, uk);
+        tr(n, n, Fk, Ft);
+        mm(n, n, 1, Fk, x, xp);
+        add(n, xp, uk, xp);                          /* xbar_{k+1|k} */
+        mm(n, n, n, Fk, P, t1);
+        mm(n, n, n, t1, Ft, t2);
+        add(n * n, t2, Qk, Pp);                      /* P_{k+1|k} */
+        if (lu_solve(n, n, Pp, t1, Gt)) return -1;   /* G^T = P_{k+1|k}^{-1} F_k P */
+        tr(n, n, Gt, G);
+        sub(n, ms + (t + 1) * n, xp, dx);
+        mm(n, n, 1, G, dx, t1);
+        add(n, x, t1, ms + t * n);
+        sub(n * n, Ps + (t + 1) * n * n, Pp, dP);
+        mm(n, n, n, G, dP, t1);
+        mm(n, n, n, t1, Gt, t2);
+        add(n * n, P, t2, Ps + t * n * n);
+    }
+    return 0;
+}
+
+/* Sequential two-filter smoother: the backward information filter of
+ * Eqs. tf_vector_pred .. tf_matrix_upd with u and d, merged with the filter
+ * by Eqs. mean_tf_combination / cov_tf_combination.  eta_out, J_out
+ * (nullable) receive eta_{k|k+1:T}, J_{k|k+1:T} (zero at k = T). */
+int orc_tv_tf(int n, int m, const double *F, const double *Q, const double *u, const double *H, const double *R,
+              const double *d, long T, const double *y, const double *mf, const double *Pf, double *ms, double *Ps,
+              double *eta_out, double *J_out) {
+    double Ft[ORC_MAXN * ORC_MAXN], Ht[ORC_MAXN * ORC_MAXN], Ri[ORC_MAXN * ORC_MAXN], HtRi[ORC_MAXN * ORC_MAXN];
+    double eta[ORC_MAXN], J[ORC_MAXN * ORC_MAXN], t1[ORC_MAXN * ORC_MAXN], t2[ORC_MAXN * ORC_MAXN];
+    double Mx[ORC_MAXN * ORC_MAXN], I[ORC_MAXN * ORC_MAXN], rhs[ORC_MAXN * (ORC_MAXN + 1)];
+    double sol[ORC_MAXN * (ORC_MAXN + 1)], uk[ORC_MAXN], dk[ORC_MAXN], yd[ORC_MAXN];
+    eye(n, I);
+    memset(eta, 0, sizeof(double) * n);          /* eta_{T|T+1:T} = 0 */
+    memset(J, 0, sizeof(double) * n * n);        /* J_{T|T+1:T}   = 0 */
+    for (long t = T - 1; t >= 0; --t) {          /* time k = t + 1 */
+        const double *x = mf + t * n, *P = Pf + t * n * n;
+        if (eta_out) memcpy(eta_out + t * n, eta, sizeof(double) * n);
+        if (J_out) memcpy(J_out + t * n * n, J, sizeof(double) * n * n);
+        /* merge: xbar_{k|T} = (I + P J)^{-1}(xbar + P eta), P_{k|T} = (I + P J)^{-1} P */
+        mm(n, n, n, P, J, t1);
+        add(n * n, I, t1, Mx);
+        mm(n, n, 1, P, eta, t2);
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) rhs[i * (n + 1) + j] = P[i * n + j];
+            rhs[i * (n + 1) + n] = x[i] + t2[i];
+        }
+        if (lu_solve(n, n + 1, Mx, rhs, sol)) return -1;
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) Ps[t * n * n + i * n + j] = sol[i * (n + 1) + j];
+            ms[t * n + i] = sol[i * (n + 1) + n];
+        }
+        if (t == 0) break;
+        /* update with y_k: eta += H_k^T R_k^{-1} (y_k - d_k), J += H_k^T R_k^{-1} H_k */
+        const double *Hk = H + t * m * n, *Rk = R + t * m * m;
+        vec_or_zero(m, d, t, dk);
+        tr(m, n, Hk, Ht);
+        if (inv(m, Rk, Ri)) return -1;
+        mm(n, m, m, Ht, Ri, HtRi);
+        sub(m, y + t * m, dk, yd);
+        mm(n, m, 1, HtRi, yd, t1);
+        add(n, eta, t1, eta);
+        mm(n, m, n, HtRi, Hk, t1);
+        add(n * n, J, t1, J);
+        /* backward prediction to time k - 1 with F_{k-1}, Q_{k-1}, u_{k-1} (record t):
+         * eta <- F^T (I + J Q)^{-1} (eta - J u),  J <- F^T (I + J Q)^{-1} J F */
+        const double *Fk = F + t * n * n, *Qk = Q + t * n * n;
+        vec_or_zero(n, u, t, uk);
+        tr(n, n, Fk, Ft);
+        mm(n, n, n, J, Qk, t1);
+        add(n * n, I, t1, Mx);
+        mm(n, n, 1, J, uk, t2);
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) rhs[i * (n + 1) + j] = J[i * n + j];
+            rhs[i * (n + 1) + n] = eta[i] - t2[i];
+        }
+        if (lu_solve(n, n + 1, Mx, rhs, sol)) return -1;
+        double JF[ORC_MAXN * ORC_MAXN], v[ORC_MAXN], MiJ[ORC_MAXN * ORC_MAXN];
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) MiJ[i * n + j] = sol[i * (n + 1) + j];
+            v[i] = sol[i * (n + 1) + n];
+        }
+        mm(n, n, 1, Ft, v, eta);
+        mm(n, n, n, MiJ, Fk, JF);
+        mm(n, n, n, Ft, JF, J);
+    }
+    return 0;
+}
+
+/* Element a_k of Eqs. pkf_init1 (first = 0) / pkf_init2 (first = 1) and
+ * pkf_init3 for one step, given that step's F_{k-1}, Q_{k-1}, u_{k-1}, H_k,
+ * R_k, d_k (u, d nullable) and y_k.  As for the time-invariant element,
+ * eta_k and J_k use S_k = H_k Q_{k-1} H_k^T + R_k for every k (eta_1, J_1
+ * never reach an output because A_1 = 0). */
+int orc_tv_filter_element(int n, int m, const double *F, const double *Q, const double *u, const double *H,
+                          const double *R, const double *d, const double *m0, const double *P0, int first,
+                          const double *yk, double *e) {
+    double *A = e, *b = e + n * n, *C = e + n * n + n, *eta = e + 2 * n * n + n, *J = e + 2 * n * n + 2 * n;
+    double Ht[ORC_MAXN * ORC_MAXN], Ft[ORC_MAXN * ORC_MAXN], t1[ORC_MAXN * ORC_MAXN], t2[ORC_MAXN * ORC_MAXN];
+    double S[ORC_MAXN * ORC_MAXN], KT[ORC_MAXN * ORC_MAXN], K[ORC_MAXN * ORC_MAXN], IKH[ORC_MAXN * ORC_MAXN];
+    double uk[ORC_MAXN], dk[ORC_MAXN], v[ORC_MAXN], QHt[ORC_MAXN * ORC_MAXN];
+    vec_or_zero(n, u, 0, uk);
+    vec_or_zero(m, d, 0, dk);
+    tr(m, n, H, Ht);
+    tr(n, n, F, Ft);
+    if (first) {
+        double xp[ORC_MAXN], Pp[ORC_MAXN * ORC_MAXN], PHt[ORC_MAXN * ORC_MAXN], KS[ORC_MAXN * ORC_MAXN];
+        mm(n, n, 1, F, m0, xp);
+        add(n, xp, uk, xp);                      /* xbar_{1|0} = F_0 xbar_{0|0} + u_0 */
+        mm(n, n, n, F, P0, t1);
+        mm(n, n, n, t1, Ft, t2);
+        add(n * n, t2, Q, Pp);                   /* P_{1|0} = F_0 P_{0|0} F_0^T + Q_0 */
+        mm(n, n, m, Pp, Ht, PHt);
+        mm(m, n, m, H, PHt, t1);
+        add(m * m, t1, R, S);                    /* S_1 = H_1 P_{1|0} H_1^T + R_1 */
+        tr(n, m, PHt, t1);
+        if (chol_solve(m, n, S, t1, KT, NULL)) return -1;
+        tr(m, n, KT, K);                         /* K_1 = P_{1|0} H_1^T S_1^{-1} */
+        memset(A, 0, sizeof(double) * n * n);    /* A_1 = 0 */
+        mm(m, n, 1, H, xp, t1);
+        sub(m, yk, t1, v);
+        sub(m, v, dk, v);
+        mm(n, m, 1, K, v, t1);
+        add(n, xp, t1, b);                       /* b_1 = xbar_{1|0} + K_1 (y_1 - H_1 xbar_{1|0} - d_1) */
+        mm(n, m, m, K, S, KS);
+        mm(n, m, n, KS, KT, t1);
+        sub(n * n, Pp, t1, C);                   /* C_1 = P_{1|0} - K_1 S_1 K_1^T */
+    } else {
+        mm(n, n, m, Q, Ht, QHt);
+        mm(m, n, m, H, QHt, t1);
+        add(m * m, t1, R, S);                    /* S_k = H_k Q_{k-1} H_k^T + R_k */
+        tr(n, m, QHt, t1);
+        if (chol_solve(m, n, S, t1, KT, NULL)) return -1;
+        tr(m, n, KT, K);                         /* K_k = Q_{k-1} H_k^T S_k^{-1} */
+        mm(n, m, n, K, H, t1);
+        eye(n, t2);
+        sub(n * n, t2, t1, IKH);
+        mm(n, n, n, IKH, F, A);                  /* A_k = (I - K_k H_k) F_{k-1} */
+        mm(m, n, 1, H, uk, t1);
+        sub(m, yk, t1, v);
+        sub(m, v, dk, v);
+        mm(n, m, 1, K, v, t1);
+        add(n, uk, t1, b);                       /* b_k = u_{k-1} + K_k (y_k - H_k u_{k-1} - d_k) */
+        mm(n, n, n, IKH, Q, C);                  /* C_k = (I - K_k H_k) Q_{k-1} */
+    }
+    {   /* Eq. pkf_init3: eta_k = F^T H^T S^{-1} (y_k - H_k u_{k-1} - d_k), J_k = F^T H^T S^{-1} H F */
+        double Sx[ORC_MAXN * ORC_MAXN], SiH[ORC_MAXN * ORC_MAXN], Siy[ORC_MAXN], HF[ORC_MAXN * ORC_MAXN];
+        double FtHt[ORC_MAXN * ORC_MAXN];
+        mm(n, n, m, Q, Ht, QHt);
+        mm(m, n, m, H, QHt, t1);
+        add(m * m, t1, R, Sx);
+        mm(m, n, 1, H, uk, t1);
+        sub(m, yk, t1, v);
+        sub(m, v, dk, v);
+        if (chol_solve(m, 1, Sx, v, Siy, NULL)) return -1;
+        mm(m, n, n, H, F, HF);
+        if (chol_solve(m, n, Sx, HF, SiH, NULL)) return -1;
+        tr(m, n, HF, FtHt);
+        mm(n, m, 1, FtHt, Siy, eta);
+        mm(n, m, n, FtHt, SiH, J);
+    }
+    return 0;
+}
+
+/* Element of Eqs. prts_init1 (last = 0, with the step's F_k, Q_k, u_k;
+ * u nullable) / prts_init2 (last = 1) from xbar_{k|k}, P_{k|k}. */
+int orc_tv_rts_element(int n, const double *F, const double *Q, const double *u, int last, const double *xk,
+                       const double *Pk, double *e) {
+    double *E = e, *g = e + n * n, *L = e + n * n + n;
+    if (last) {
+        memset(E, 0, sizeof(double) * n * n);
+        memcpy(g, xk, sizeof(double) * n);
+        memcpy(L, Pk, sizeof(double) * n * n);
+        return 0;
+    }
+    double Ft[ORC_MAXN * ORC_MAXN], t1[ORC_MAXN * ORC_MAXN], t2[ORC_MAXN * ORC_MAXN], Pp[ORC_MAXN * ORC_MAXN];
+    double Et[ORC_MAXN * ORC_MAXN], v[ORC_MAXN], w[ORC_MAXN], rE[ORC_MAXN * ORC_MAXN], uk[ORC_MAXN];
+    vec_or_zero(n, u, 0, uk);
+    tr(n, n, F, Ft);
+    mm(n, n, n, F, Pk, t1);
+    mm(n, n, n, t1, Ft, t2);
+    add(n * n, t2, Q, Pp);                         /* F_k P F_k^T + Q_k */
+    if (lu_solve(n, n, Pp, t1, Et)) return -1;
+    tr(n, n, Et, rE);                               /* E_k = P F_k^T (F_k P F_k^T + Q_k)^{-1} */
+    mm(n, n, 1, F, xk, v);
+    add(n, v, uk, v);
+    mm(n, n, 1, rE, v, w);
+    sub(n, xk, w, g);                               /* g_k = xbar - E_k (F_k xbar + u_k) */
+    mm(n, n, n, rE, t1, t2);
+    sub(n * n, Pk, t2, L);                          /* L_k = P - E_k F_k P */
+    memcpy(E, rE, sizeof(double) * n * n);
+    return 0;
+}
