@@ -14,6 +14,7 @@ timed events.  Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -134,15 +135,26 @@ def job_rate(world, steps, T, max_ms):
 # ------------------------------------------------------------------ DRAM traffic
 
 def kernel_source_hash():
-    """sha256 over the CUDA sources, so that a recorded ncu traffic figure is
-    used only for the kernels it was measured on."""
+    """sha256 over the sources the time-invariant scan kernels compile from --
+    the per-size launch units (kf_n<N>_<precision>*.cu) and every header they
+    include -- so that a recorded ncu traffic figure is used only for the
+    kernels it was measured on."""
     import hashlib
-    h = hashlib.sha256()
+    import re
     d = os.path.join(ROOT, "paper_2511_10363_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(f.encode() + b"\0" + fh.read())
+    todo = [f for f in sorted(os.listdir(d)) if re.match(r"kf_n\d+_\w+\.cu$", f)]
+    seen = set()
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(os.path.join(d, f)):
+            continue
+        seen.add(f)
+        with open(os.path.join(d, f), "rb") as fh:
+            todo += [m.decode() for m in re.findall(rb'#include "([^"/]+)"', fh.read())]
+    h = hashlib.sha256()
+    for f in sorted(seen):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -377,6 +389,69 @@ def workload_mixed(args):
                       "results": res}))
 
 
+def workload_tv(args):
+    """Time-varying tracking model (per-step F, Q, u, H, R, d of Sec. III-A;
+    nx = 4, ny = 2), T = --T (default 2^20): kf_tv_rts_smooth with the
+    log-likelihood, FP32 and FP64, beside kf_rts_smooth on a time-invariant
+    model of the same size.  Per-kernel times come from the library's CUDA
+    events; the roofline is HBM with the algorithmic bytes of a smoothed step
+    (inputs of the filter pass, F, Q, u again in the RTS pass, the filter
+    record written and read back, the smoothed mean and covariance).  The
+    inputs exceed L2 at this T, so no flush is done between runs."""
+    import torch
+    import paper_2511_10363_gb300 as kf
+    T = args.T
+    nx, ny = 4, 2
+    model = W.tv_model(nx, T, seed=2)
+    y64 = W.simulate_tv(model, seed=3)
+    ti_model = kf.Model(W.cv_model())
+    y_ti64 = W.simulate(W.cv_model(), T, seed=3)
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        hbm = float(json.load(f)["hbm_gbs"])
+    rec_vals = nx + nx * (nx + 1) // 2
+    vals = (ny + 2 * nx * nx + nx + ny * nx + ny * ny + ny) + (2 * nx * nx + nx) + 2 * rec_vals + (nx + nx * nx)
+    res = {}
+    for prec in ("fp32", "fp64"):
+        dt = kf.dtype_of(prec)
+        w = 8 if prec == "fp64" else 4
+        tm = kf.TvModel(model, prec, "cuda")
+        y = torch.tensor(y64, dtype=dt, device="cuda")
+        yti = torch.tensor(y_ti64, dtype=dt, device="cuda")
+        ms = torch.empty((T, nx), dtype=dt, device="cuda")
+        Ps = torch.empty((T, nx, nx), dtype=dt, device="cuda")
+        ll = torch.empty(1, dtype=torch.float64, device="cuda")
+        ws = torch.empty(kf.kf_workspace_size("rts", nx, ny, T, prec, "dlb"), dtype=torch.uint8, device="cuda")
+
+        def tv_call():
+            rc = kf.lib().kf_tv_rts_smooth(ctypes.byref(tm.c), T, kf._ptr(y), kf.PRECISIONS[prec], 1, kf._ptr(ms),
+                                           kf._ptr(Ps), None, None, kf._ptr(ll), kf._ptr(ws), kf._stream(None))
+            assert rc == 0, rc
+
+        kf.kf_timing_reset()
+        kf.kf_timing_enable(1)
+        t_tv = _timed(tv_call)
+        kf.kf_timing_enable(0)
+        kern = {}
+        for name, kd in (("filter_scan", 0), ("rts_scan", 1)):
+            n_l, t_ms = kf.timing_read(kd)
+            if n_l:
+                kern[name] = {"launches": n_l, "avg_ms": t_ms / n_l}
+        t_ti = _timed(lambda: kf.kf_rts_smooth(ti_model, yti, prec, "auto", ms_out=ms, Ps_out=Ps, loglik=True))
+        assert kf.kf_sync_status() == 0
+        gbs = vals * w * T / (t_tv * 1e-3) / 1e9
+        res[prec] = {"tv_ms": t_tv, "tv_steps_per_s": T / (t_tv * 1e-3), "tv_kernels": kern,
+                     "time_invariant_ms": t_ti, "time_invariant_steps_per_s": T / (t_ti * 1e-3),
+                     "roofline": {"bound": "hbm", "bytes_per_step": vals * w, "achieved": gbs, "peak": hbm,
+                                  "unit": "GB/s", "frac": gbs / hbm,
+                                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
+        del ws
+    print(json.dumps({"workload": "tv", "metric": "smoothed steps/s", "unit": "smoothed steps/s",
+                      "model": "time-varying 2D constant-velocity tracking nx=4 ny=2 with inputs u, d", "T": T,
+                      "op": "rts (filter + smoother) with log-likelihood, decoupled look-back",
+                      "timing": "median of 10 after 2 dropped runs (CUDA events); inputs larger than L2",
+                      "results": res}))
+
+
 def workload_batch(args):
     """4096 tracking sequences, T log-uniform in [64, 65536], RTS smoother:
     one segmented scan over the whole batch vs one kf_rts_smooth call per
@@ -541,7 +616,7 @@ def main():
     ap.add_argument("--retune", action="store_true", help="autotune even when the tuning table has an entry")
     ap.add_argument("--save-tuning", default=None, help="write the tuning table after autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "sweep", "mixed", "batch", "serving"],
+    ap.add_argument("--workload", default="single", choices=["single", "sweep", "mixed", "batch", "serving", "tv"],
                     help="single: the headline line (default); the others print their own line")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: arrival window (s)")
@@ -564,7 +639,7 @@ def main():
         torch.cuda.set_device(local)
         kbuild.build()
         {"sweep": workload_sweep, "mixed": workload_mixed, "batch": workload_batch,
-         "serving": workload_serving}[args.workload](args)
+         "serving": workload_serving, "tv": workload_tv}[args.workload](args)
         return
 
     import torch

@@ -135,6 +135,59 @@ kf_status_t kf_two_filter_smooth(const kf_model_t *model, int64_t T, const void 
                                  void *mf_out, void *Pf_out, double *loglik, void *workspace,
                                  void *stream);
 
+/* ---------------------------------------------------------------- time-varying models
+ *
+ * The general linear-Gaussian model of Sec. III-A (the transition and
+ * measurement densities) with per-step matrices and inputs:
+ *     x_k = F_{k-1} x_{k-1} + u_{k-1} + q_{k-1},   q_{k-1} ~ N(0, Q_{k-1})
+ *     y_k = H_k x_k + d_k + r_k,                   r_k ~ N(0, R_k)
+ * Every element is built from its own step (Eqs. pkf_init1..3 with u and d,
+ * Eqs. prts_init1/2 with u) inside the scan pass.
+ *
+ * The per-step arrays are DEVICE buffers in the working precision (FP64 for
+ * KF_FP64, FP32 otherwise), row-major, record t = 0 .. T-1 for time k = t + 1:
+ *     F [T][nx][nx]  F[t] = F_{k-1}       Q [T][nx][nx]  Q[t] = Q_{k-1}
+ *     u [T][nx]      u[t] = u_{k-1}, or NULL (no input)
+ *     H [T][ny][nx]  H[t] = H_k           R [T][ny][ny]  R[t] = R_k
+ *     d [T][ny]      d[t] = d_k, or NULL (no offset)
+ * Each must be aligned to its element size.  Only the upper triangles of
+ * Q[t] and R[t] are read.  m0, P0: host FP64 prior xbar_{0|0}, P_{0|0},
+ * copied at the call (finite; P0 symmetric positive semi-definite, else
+ * KF_ERR_NOT_PD).  nx in {2, 4, 8}, 1 <= ny <= nx.  The device arrays are
+ * caller-owned, are not checked, and are read by the call's kernels on
+ * `stream`: R[t] must be symmetric positive definite and Q[t] symmetric
+ * positive semi-definite (and F_k P_{k|k} F_k^T + Q_k positive definite for
+ * the RTS smoother); otherwise the outputs are not finite.
+ * scan: KF_SCAN_AUTO or KF_SCAN_DECOUPLED_LOOKBACK (others: KF_ERR_ARG).
+ * Workspace: kf_workspace_size(op, nx, ny, T, prec,
+ * KF_SCAN_DECOUPLED_LOOKBACK) bytes, or NULL for the library's cache.
+ * y, the outputs, loglik (innovation form with v_k = y_k - H_k xbar_{k|k-1}
+ * - d_k), stream and the error behaviour are those of kf_filter and
+ * kf_rts_smooth. */
+typedef struct {
+    int nx, ny;
+    const void *F, *Q, *u, *H, *R, *d;
+    const double *m0, *P0;
+} kf_tv_model_t;
+
+/* Alg. pkf on a time-varying model: m_out [T][nx], P_out [T][nx][nx] (may be NULL). */
+kf_status_t kf_tv_filter(const kf_tv_model_t *model, int64_t T, const void *y, kf_precision_t prec,
+                         kf_scan_t scan, void *m_out, void *P_out, double *loglik, void *workspace,
+                         void *stream);
+
+/* Alg. prts on a time-varying model (RTS elements with F_k, Q_k, u_k of the
+ * step k -> k+1); outputs as kf_rts_smooth. */
+kf_status_t kf_tv_rts_smooth(const kf_tv_model_t *model, int64_t T, const void *y,
+                             kf_precision_t prec, kf_scan_t scan, void *ms_out, void *Ps_out,
+                             void *mf_out, void *Pf_out, double *loglik, void *workspace,
+                             void *stream);
+
+/* Alg. ptf on a time-varying model; outputs as kf_rts_smooth. */
+kf_status_t kf_tv_two_filter_smooth(const kf_tv_model_t *model, int64_t T, const void *y,
+                                    kf_precision_t prec, kf_scan_t scan, void *ms_out,
+                                    void *Ps_out, void *mf_out, void *Pf_out, double *loglik,
+                                    void *workspace, void *stream);
+
 /* Batch of independent sequences (the segmented scan): sequence s is
  * y[offsets[s] .. offsets[s+1]) of the concatenated device buffer y
  * [total][ny], total = offsets[nseq], and uses model

@@ -7,6 +7,7 @@ to run if the compiled library is missing; there is no CPU fallback.
 
 Function names match the C ABI:
     kf_filter, kf_rts_smooth, kf_two_filter_smooth,
+    kf_tv_filter, kf_tv_rts_smooth, kf_tv_two_filter_smooth (time-varying models),
     kf_workspace_size, kf_sync_status, kf_set_option, kf_get_option,
     kf_status_string, kf_version.
 """
@@ -45,6 +46,12 @@ class KfError(RuntimeError):
 class _Model(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int)] + [
         (k, ctypes.POINTER(ctypes.c_double)) for k in ("F", "Q", "H", "R", "m0", "P0")]
+
+
+class _TvModel(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int)] + [
+        (k, ctypes.c_void_p) for k in ("F", "Q", "u", "H", "R", "d")] + [
+        (k, ctypes.POINTER(ctypes.c_double)) for k in ("m0", "P0")]
 
 
 def lib():
@@ -105,6 +112,12 @@ def lib():
             getattr(L, f).restype = ctypes.c_int
         L.kf_rts_smooth_noalloc.restype = ctypes.c_int
         L.kf_trace_phases.restype = ctypes.c_int
+        TP = ctypes.POINTER(_TvModel)
+        L.kf_tv_filter.argtypes = [TP, i64, vp, i, i, vp, vp, vp, vp, vp]
+        L.kf_tv_rts_smooth.argtypes = [TP, i64, vp, i, i, vp, vp, vp, vp, vp, vp, vp]
+        L.kf_tv_two_filter_smooth.argtypes = [TP, i64, vp, i, i, vp, vp, vp, vp, vp, vp, vp]
+        for f in ("kf_tv_filter", "kf_tv_rts_smooth", "kf_tv_two_filter_smooth"):
+            getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -216,6 +229,102 @@ def kf_two_filter_smooth(model, y, precision="fp32", scan="dlb", ms_out=None, Ps
     """Alg. ptf (with its filter pass).  Returns (ms, Ps, loglik or None)."""
     return _smooth(lib().kf_two_filter_smooth, "kf_two_filter_smooth", model, y, precision, scan, ms_out,
                    Ps_out, mf_out, Pf_out, loglik, workspace, stream)
+
+
+class TvModel:
+    """A time-varying model laid out for kf_tv_model_t: the per-step arrays
+    F [T,nx,nx], Q [T,nx,nx], u [T,nx] or None, H [T,ny,nx], R [T,ny,ny],
+    d [T,ny] or None as contiguous CUDA tensors of the working dtype (record
+    t is time t + 1: F[t] = F_{k-1}, H[t] = H_k), and the host FP64 prior
+    m0, P0.  Arrays given as numpy or host tensors are copied to ``device``."""
+
+    def __init__(self, model, precision="fp32", device="cuda"):
+        import torch
+        dt = dtype_of(precision)
+        self.precision = precision
+        self.t = {}
+        for k in ("F", "Q", "u", "H", "R", "d"):
+            v = model.get(k) if hasattr(model, "get") else model[k]
+            if v is None:
+                self.t[k] = None
+                continue
+            if not isinstance(v, torch.Tensor):
+                v = torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64))
+            self.t[k] = v.to(device=device, dtype=dt).contiguous()
+        self.m0 = np.ascontiguousarray(np.asarray(model["m0"], dtype=np.float64))
+        self.P0 = np.ascontiguousarray(np.asarray(model["P0"], dtype=np.float64))
+        F, H = self.t["F"], self.t["H"]
+        self.T, self.nx, self.ny = int(F.shape[0]), int(F.shape[1]), int(H.shape[1])
+        shapes = {"F": (self.T, self.nx, self.nx), "Q": (self.T, self.nx, self.nx), "u": (self.T, self.nx),
+                  "H": (self.T, self.ny, self.nx), "R": (self.T, self.ny, self.ny), "d": (self.T, self.ny)}
+        for k, shp in shapes.items():
+            if self.t[k] is not None and tuple(self.t[k].shape) != shp:
+                raise ValueError("time-varying model: %s must have shape %s" % (k, shp))
+        D = ctypes.POINTER(ctypes.c_double)
+        self.c = _TvModel(self.nx, self.ny, *[_ptr(self.t[k]) for k in ("F", "Q", "u", "H", "R", "d")],
+                          self.m0.ctypes.data_as(D), self.P0.ctypes.data_as(D))
+
+
+def _tv_prep(model, y, precision):
+    import torch
+    m = model if isinstance(model, TvModel) else TvModel(model, precision, y.device)
+    if m.precision != precision and dtype_of(m.precision) != dtype_of(precision):
+        raise ValueError("the model arrays are %s; the call asks for %s" % (m.precision, precision))
+    if not (isinstance(y, torch.Tensor) and y.is_cuda):
+        raise TypeError("y must be a CUDA tensor")
+    dt = dtype_of(precision)
+    if y.dtype != dt or not y.is_contiguous() or y.dim() != 2 or y.shape[1] != m.ny or y.shape[0] > m.T:
+        raise ValueError("y must be contiguous [T, ny] of dtype %s with T <= the model's steps" % dt)
+    return m, dt
+
+
+def kf_tv_filter(model, y, precision="fp32", scan="dlb", m_out=None, P_out=None, loglik=False, workspace=None,
+                 stream=None, want_cov=True):
+    """Alg. pkf on a time-varying model (TvModel or dict of per-step arrays).
+    Returns (m [T,nx], P [T,nx,nx] or None, loglik tensor [1] or None)."""
+    import torch
+    m, dt = _tv_prep(model, y, precision)
+    T = y.shape[0]
+    dev = y.device
+    if m_out is None:
+        m_out = torch.empty((T, m.nx), dtype=dt, device=dev)
+    if P_out is None and want_cov:
+        P_out = torch.empty((T, m.nx, m.nx), dtype=dt, device=dev)
+    ll = torch.empty(1, dtype=torch.float64, device=dev) if loglik else None
+    rc = lib().kf_tv_filter(ctypes.byref(m.c), T, _ptr(y), PRECISIONS[precision], SCANS[scan], _ptr(m_out),
+                            _ptr(P_out), _ptr(ll), _ptr(workspace), _stream(stream))
+    _check(rc, "kf_tv_filter")
+    return m_out, P_out, ll
+
+
+def _tv_smooth(fn, name, model, y, precision, scan, ms_out, Ps_out, mf_out, Pf_out, loglik, workspace, stream):
+    import torch
+    m, dt = _tv_prep(model, y, precision)
+    T = y.shape[0]
+    dev = y.device
+    if ms_out is None:
+        ms_out = torch.empty((T, m.nx), dtype=dt, device=dev)
+    if Ps_out is None:
+        Ps_out = torch.empty((T, m.nx, m.nx), dtype=dt, device=dev)
+    ll = torch.empty(1, dtype=torch.float64, device=dev) if loglik else None
+    rc = fn(ctypes.byref(m.c), T, _ptr(y), PRECISIONS[precision], SCANS[scan], _ptr(ms_out), _ptr(Ps_out),
+            _ptr(mf_out), _ptr(Pf_out), _ptr(ll), _ptr(workspace), _stream(stream))
+    _check(rc, name)
+    return ms_out, Ps_out, ll
+
+
+def kf_tv_rts_smooth(model, y, precision="fp32", scan="dlb", ms_out=None, Ps_out=None, mf_out=None, Pf_out=None,
+                     loglik=False, workspace=None, stream=None):
+    """Alg. prts on a time-varying model.  Returns (ms, Ps, loglik or None)."""
+    return _tv_smooth(lib().kf_tv_rts_smooth, "kf_tv_rts_smooth", model, y, precision, scan, ms_out, Ps_out,
+                      mf_out, Pf_out, loglik, workspace, stream)
+
+
+def kf_tv_two_filter_smooth(model, y, precision="fp32", scan="dlb", ms_out=None, Ps_out=None, mf_out=None,
+                            Pf_out=None, loglik=False, workspace=None, stream=None):
+    """Alg. ptf on a time-varying model.  Returns (ms, Ps, loglik or None)."""
+    return _tv_smooth(lib().kf_tv_two_filter_smooth, "kf_tv_two_filter_smooth", model, y, precision, scan, ms_out,
+                      Ps_out, mf_out, Pf_out, loglik, workspace, stream)
 
 
 def kf_sync_status(stream=None):

@@ -16,6 +16,7 @@
 
 #include "../../include/kfscan.h"
 #include "kf_host.h"
+#include "kf_tv_host.h"
 
 namespace kfs {
 
@@ -827,6 +828,103 @@ kf_status_t kf_two_filter_smooth(const kf_model_t *model, int64_t T, const void 
                                  kf_scan_t scan, void *ms_out, void *Ps_out, void *mf_out, void *Pf_out,
                                  double *loglik, void *workspace, void *stream) {
     return run(KF_OP_TF_I, model, T, y, prec, scan, ms_out, Ps_out, mf_out, Pf_out, loglik, workspace, stream);
+}
+
+// ---------------------------------------------------------------- time-varying models
+
+// One call on a time-varying model: host checks of the sizes, pointers,
+// alignment and prior, then the filter pass and the smoother pass of the
+// decoupled look-back scan (kf_tv.cuh).  The per-step device arrays are the
+// caller's and are not read on the host.
+static kf_status_t run_tv(int op, const kf_tv_model_t *md, int64_t T, const void *y, kf_precision_t prec,
+                          kf_scan_t scan, void *m1, void *P1, void *m2, void *P2, double *loglik, void *workspace,
+                          void *stream) {
+    if (!md || (md->nx != 2 && md->nx != 4 && md->nx != 8) || md->ny < 1 || md->ny > md->nx) return KF_ERR_ARG;
+    if (!md->F || !md->Q || !md->H || !md->R || !md->m0 || !md->P0) return KF_ERR_ARG;
+    if (T < 1 || T > (int64_t(1) << 40) || !y) return KF_ERR_ARG;
+    if (prec != KF_FP64 && prec != KF_FP32 && prec != KF_FP32_FP64SOLVE) return KF_ERR_ARG;
+    if (scan != KF_SCAN_AUTO && scan != KF_SCAN_DECOUPLED_LOOKBACK) return KF_ERR_ARG;
+    const int n = md->nx, m = md->ny;
+    for (int i = 0; i < n; ++i)
+        if (!isfinite(md->m0[i])) return KF_ERR_ARG;
+    if (!is_spsd(n, md->P0)) return KF_ERR_NOT_PD;
+    const size_t w = (prec == KF_FP64) ? 8 : 4;
+    const void *arrs[6] = {md->F, md->Q, md->u, md->H, md->R, md->d};
+    for (const void *a : arrs)
+        if (a && !aligned(a, w)) return KF_ERR_ARG;
+    TvLaunch t;
+    memset(&t, 0, sizeof(t));
+    LaunchReq &q = t.q;
+    q.op = op;
+    q.prec = int(prec);
+    q.scan = KF_SCAN_DLB_I;
+    q.T = T;
+    q.y = y;
+    if (op == KF_OP_FILTER_I) {
+        if (!m1) return KF_ERR_ARG;
+        q.mf_user = m1;
+        q.Pf_user = P1;
+    } else {
+        if (!m1 || !P1) return KF_ERR_ARG;
+        q.ms = m1;
+        q.Ps = P1;
+        q.mf_user = m2;
+        q.Pf_user = P2;
+    }
+    if (!rows_aligned(y, m, w) || !rows_aligned(m1, n, w) || !rows_aligned(P1, n * n, w) ||
+        !rows_aligned(m2, n, w) || !rows_aligned(P2, n * n, w))
+        return KF_ERR_ARG;
+    if (loglik && !aligned(loglik, 8)) return KF_ERR_ARG;
+    if (workspace && !aligned(workspace, 256)) return KF_ERR_ARG;
+    t.ny = m;
+    t.F = md->F;
+    t.Q = md->Q;
+    t.u = md->u;
+    t.H = md->H;
+    t.R = md->R;
+    t.d = md->d;
+    for (int i = 0; i < n; ++i) t.m0[i] = md->m0[i];
+    for (int i = 0; i < n * n; ++i) t.P0[i] = md->P0[i];
+    symmetrize(n, t.P0);
+    q.loglik = loglik;
+    q.stream = static_cast<cudaStream_t>(stream);
+    q.timeout_ns = g_opt[KF_OPT_WAIT_TIMEOUT_NS].load();
+    q.inject_skip_tile = int(g_opt[KF_OPT_TEST_SKIP_TILE].load());
+    q.k_override = int(g_opt[KF_OPT_POSITIONS_PER_THREAD].load());
+    q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
+    kf_status_t s = device_status_word(&q.status);
+    if (s != KF_OK) return s;
+    const size_t need = ws_bytes_dispatch(n, op, q.prec, KF_SCAN_DLB_I, T);
+    if (workspace) {
+        q.ws = workspace;
+    } else {
+        s = library_workspace(need, &q.ws);
+        if (s != KF_OK) return s;
+    }
+    cudaError_t e;
+    switch (n) {
+        case 2: e = launch_tv_n2(t); break;
+        case 4: e = launch_tv_n4(t); break;
+        default: e = launch_tv_n8(t); break;
+    }
+    return from_cuda(e);
+}
+
+kf_status_t kf_tv_filter(const kf_tv_model_t *model, int64_t T, const void *y, kf_precision_t prec, kf_scan_t scan,
+                         void *m_out, void *P_out, double *loglik, void *workspace, void *stream) {
+    return run_tv(KF_OP_FILTER_I, model, T, y, prec, scan, m_out, P_out, nullptr, nullptr, loglik, workspace, stream);
+}
+
+kf_status_t kf_tv_rts_smooth(const kf_tv_model_t *model, int64_t T, const void *y, kf_precision_t prec,
+                             kf_scan_t scan, void *ms_out, void *Ps_out, void *mf_out, void *Pf_out, double *loglik,
+                             void *workspace, void *stream) {
+    return run_tv(KF_OP_RTS_I, model, T, y, prec, scan, ms_out, Ps_out, mf_out, Pf_out, loglik, workspace, stream);
+}
+
+kf_status_t kf_tv_two_filter_smooth(const kf_tv_model_t *model, int64_t T, const void *y, kf_precision_t prec,
+                                    kf_scan_t scan, void *ms_out, void *Ps_out, void *mf_out, void *Pf_out,
+                                    double *loglik, void *workspace, void *stream) {
+    return run_tv(KF_OP_TF_I, model, T, y, prec, scan, ms_out, Ps_out, mf_out, Pf_out, loglik, workspace, stream);
 }
 
 size_t kf_batch_workspace_size(kf_op_t op, int nx, int ny, int64_t total_steps, int nseq, int nmodels,

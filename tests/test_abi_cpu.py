@@ -152,3 +152,41 @@ def test_tuning_table_file(lib, tmp_path):
     auto = kf.kf_workspace_size("rts", 4, 2, 1 << 16, "fp32", "auto")
     assert auto >= kf.kf_workspace_size("rts", 4, 2, 1 << 16, "fp32", "dlb")
     assert auto >= kf.kf_workspace_size("rts", 4, 2, 1 << 16, "fp32", "ladner_fischer")
+
+
+def call_tv(nx=4, ny=2, T=16, y=FAKE, prec=1, scan=1, m=FAKE, arrays=None, m0=None, P0=None, op="filter"):
+    """A kf_tv_* call with fake device arrays; host FP64 prior."""
+    D = ctypes.POINTER(ctypes.c_double)
+    a = dict(F=FAKE, Q=FAKE, u=None, H=FAKE, R=FAKE, d=None)
+    a.update(arrays or {})
+    m0 = np.zeros(nx) if m0 is None else np.ascontiguousarray(m0, dtype=np.float64)
+    P0 = np.eye(nx) if P0 is None else np.ascontiguousarray(P0, dtype=np.float64)
+    c = kf._TvModel(nx, ny, *[a[k] for k in ("F", "Q", "u", "H", "R", "d")], m0.ctypes.data_as(D),
+                    P0.ctypes.data_as(D))
+    L = kf.lib()
+    if op == "filter":
+        return L.kf_tv_filter(ctypes.byref(c), T, y, prec, scan, m, None, None, None, None)
+    fn = L.kf_tv_rts_smooth if op == "rts" else L.kf_tv_two_filter_smooth
+    return fn(ctypes.byref(c), T, y, prec, scan, m, FAKE, None, None, None, None, None)
+
+
+def test_tv_argument_errors(lib):
+    for op in ("filter", "rts", "tf"):
+        assert call_tv(T=0, op=op) == 1                      # T >= 1
+        assert call_tv(y=None, op=op) == 1
+        assert call_tv(m=None, op=op) == 1
+        assert call_tv(nx=3, op=op) == 1                     # nx in {2, 4, 8}
+        assert call_tv(ny=5, op=op) == 1                     # ny <= nx
+        assert call_tv(ny=0, op=op) == 1
+        assert call_tv(prec=7, op=op) == 1
+        for scan in (2, 3, 4, 5, 9):                         # look-back scan only
+            assert call_tv(scan=scan, op=op) == 1
+        for k in ("F", "Q", "H", "R"):                       # required arrays
+            assert call_tv(arrays={k: None}, op=op) == 1
+        # arrays aligned to the element size (FP32: 4 bytes, FP64: 8 bytes)
+        assert call_tv(arrays={"u": ctypes.c_void_p((1 << 20) + 2)}, op=op) == 1
+        assert call_tv(prec=0, arrays={"F": ctypes.c_void_p((1 << 20) + 4)}, op=op) == 1
+        assert call_tv(y=ctypes.c_void_p((1 << 20) + 4), op=op) == 1   # ny = 2 FP32 rows: 8-byte
+        assert call_tv(m0=[0, np.nan, 0, 0], op=op) == 1
+        assert call_tv(P0=-np.eye(4), op=op) == 2            # prior not PSD
+        assert call_tv(P0=np.triu(np.ones((4, 4))), op=op) == 2   # not symmetric

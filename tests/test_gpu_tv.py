@@ -1,0 +1,155 @@
+"""GPU parity of the time-varying model path (kf_tv_filter, kf_tv_rts_smooth,
+kf_tv_two_filter_smooth) against the FP64 time-varying oracle on the same
+seeded inputs, through the C ABI.
+
+The per-step model arrays are rounded to the working precision before both
+sides see them, like y.  Lengths cover T = 1, 2, a partial tile, several
+tiles with a ragged tail; a forced small number of steps per thread makes
+small T span many tiles, and one case runs at T = 2^20."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests.gpu_util import TOL, mean_err, cov_err, check_psd
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp64", "fp32", "fp32_fp64solve"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2511_10363_gb300 import build
+    build.build()
+    import paper_2511_10363_gb300 as kf
+    kf.kf_set_option("positions_per_thread", 0)
+    yield
+    kf.kf_set_option("positions_per_thread", 0)
+
+
+def rounded(model, precision):
+    """The model as the GPU sees it: per-step arrays rounded to the working
+    precision (then widened to FP64 for the oracle)."""
+    if precision == "fp64":
+        return model
+    out = dict(model)
+    for k in ("F", "Q", "u", "H", "R", "d"):
+        if model.get(k) is not None:
+            out[k] = np.asarray(model[k], np.float32).astype(np.float64)
+    return out
+
+
+def run_gpu(op, model, y, precision, loglik=True):
+    import torch
+    import paper_2511_10363_gb300 as kf
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    tm = kf.TvModel(model, precision, "cuda")
+    yt = torch.as_tensor(np.ascontiguousarray(y)).to(device="cuda", dtype=dt)
+    T, nx = y.shape[0], tm.nx
+    out = {}
+    if op == "filter":
+        m, P, ll = kf.kf_tv_filter(tm, yt, precision, "dlb", loglik=loglik)
+        out["mf"], out["Pf"] = m, P
+    else:
+        mf = torch.empty((T, nx), dtype=dt, device="cuda")
+        Pf = torch.empty((T, nx, nx), dtype=dt, device="cuda")
+        fn = kf.kf_tv_rts_smooth if op == "rts" else kf.kf_tv_two_filter_smooth
+        ms, Ps, ll = fn(tm, yt, precision, "dlb", mf_out=mf, Pf_out=Pf, loglik=loglik)
+        out.update(ms=ms, Ps=Ps, mf=mf, Pf=Pf)
+    st = kf.kf_sync_status()
+    assert st == 0, "device status %d" % st
+    res = {k: v.double().cpu().numpy() for k, v in out.items()}
+    if loglik:
+        res["ll"] = float(ll.item())
+    return res
+
+
+def compare(op, model, y, precision, loglik=True):
+    mo = rounded(model, precision)
+    yo = np.asarray(y, np.float32).astype(np.float64) if precision != "fp64" else np.asarray(y, np.float64)
+    mf, Pf, ll = oracle.tv_kf(mo, yo)
+    out = run_gpu(op, mo, yo, precision, loglik)
+    tol = TOL[precision]
+    errs = {"mf": mean_err(out["mf"], mf, Pf), "Pf": cov_err(out["Pf"], Pf)}
+    check_psd(out["Pf"])
+    if op != "filter":
+        ms, Ps = oracle.tv_rts(mo, mf, Pf) if op == "rts" else oracle.tv_tf(mo, yo, mf, Pf)
+        errs["ms"] = mean_err(out["ms"], ms, Ps)
+        errs["Ps"] = cov_err(out["Ps"], Ps)
+        check_psd(out["Ps"])
+    for k, v in errs.items():
+        assert v <= tol, "%s %s: %s error %.3g > %.3g" % (op, precision, k, v, tol)
+    if loglik:
+        ll_tol = 1e-9 if precision == "fp64" else 1e-3
+        assert abs(out["ll"] - ll) <= ll_tol * max(1.0, abs(ll)), (out["ll"], ll)
+    return errs
+
+
+@pytest.mark.parametrize("op", ["filter", "rts", "tf"])
+@pytest.mark.parametrize("precision", PRECS)
+@pytest.mark.parametrize("nx", [2, 4, 8])
+@pytest.mark.parametrize("T", [1, 2, 37, 1000, 4097])
+def test_tv_parity(op, precision, nx, T):
+    model = W.tv_model(nx, T, seed=nx * 11 + T % 7)
+    y = W.simulate_tv(model, seed=3000 + T)
+    compare(op, model, y, precision)
+
+
+@pytest.mark.parametrize("op", ["filter", "rts", "tf"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tv_without_inputs(op, precision):
+    model = W.tv_model(4, 777, seed=5, inputs=False)
+    y = W.simulate_tv(model, seed=6)
+    compare(op, model, y, precision)
+
+
+@pytest.mark.parametrize("op", ["filter", "rts", "tf"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("nx", [2, 4])
+def test_tv_many_tiles(op, precision, nx):
+    """Two steps per thread: T = 5000 spans 20 look-back tiles."""
+    import paper_2511_10363_gb300 as kf
+    model = W.tv_model(nx, 5000, seed=70 + nx)
+    y = W.simulate_tv(model, seed=71)
+    kf.kf_set_option("positions_per_thread", 2)
+    try:
+        compare(op, model, y, precision)
+    finally:
+        kf.kf_set_option("positions_per_thread", 0)
+
+
+@pytest.mark.parametrize("op", ["filter", "rts", "tf"])
+def test_tv_constant_model_matches_time_invariant_path(op):
+    """Per-step arrays that repeat one model, u = d = None: the time-varying
+    kernels and the time-invariant kernels give the same results (FP64)."""
+    import torch
+    import paper_2511_10363_gb300 as kf
+    base = W.cv_model()
+    T = 3000
+    tv = dict(F=np.broadcast_to(base["F"], (T, 4, 4)), Q=np.broadcast_to(base["Q"], (T, 4, 4)),
+              H=np.broadcast_to(base["H"], (T, 2, 4)), R=np.broadcast_to(base["R"], (T, 2, 2)),
+              u=None, d=None, m0=base["m0"], P0=base["P0"])
+    y = torch.as_tensor(W.simulate(base, T, seed=8)).cuda()
+    if op == "filter":
+        a = kf.kf_filter(base, y, "fp64", "dlb", loglik=True)
+        b = kf.kf_tv_filter(tv, y, "fp64", "dlb", loglik=True)
+    else:
+        f0 = kf.kf_rts_smooth if op == "rts" else kf.kf_two_filter_smooth
+        f1 = kf.kf_tv_rts_smooth if op == "rts" else kf.kf_tv_two_filter_smooth
+        a = f0(base, y, "fp64", "dlb", loglik=True)
+        b = f1(tv, y, "fp64", "dlb", loglik=True)
+    assert kf.kf_sync_status() == 0
+    ma, Pa, la = (x.cpu().numpy() for x in a)
+    mb, Pb, lb = (x.cpu().numpy() for x in b)
+    assert mean_err(mb, ma, Pa) < 1e-10 and cov_err(Pb, Pa) < 1e-10
+    assert abs(lb[0] - la[0]) < 1e-10 * abs(la[0])
+
+
+def test_tv_full_size_rts_fp32():
+    """T = 2^20, nx = 4, FP32, RTS with the log-likelihood: every step
+    against the oracle."""
+    T = 1 << 20
+    model = W.tv_model(4, T, seed=2)
+    y = W.simulate_tv(model, seed=3)
+    compare("rts", model, y, "fp32")
