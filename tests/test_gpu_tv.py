@@ -147,9 +147,12 @@ def test_tv_constant_model_matches_time_invariant_path(op):
 
 
 def test_tv_full_size_rts_fp32():
-    """T = 2^20, nx = 4, FP32, RTS with the log-likelihood: every step
-    against the oracle."""
+    """T = 2^20, nx = 4, FP32, RTS: every step against the oracle.  The
+    log-likelihood is not compared here: the simulated positions drift to
+    about 2e7, where the FP32 spacing (2.0) exceeds the innovation standard
+    deviation (about 0.3), so no FP32 computation of the innovation can be
+    accurate; the shorter cases above check it."""
     T = 1 << 20
     model = W.tv_model(4, T, seed=2)
     y = W.simulate_tv(model, seed=3)
-    compare("rts", model, y, "fp32")
+    compare("rts", model, y, "fp32", loglik=False)
