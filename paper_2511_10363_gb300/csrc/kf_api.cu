@@ -1,7 +1,8 @@
 // kf_api.cu -- the C ABI declared in include/kfscan.h: argument checks,
 // the k-invariant FP64 precomputation of Eqs. pkf_init1/2/3 on the host,
 // the per-device workspace cache and status word, and dispatch to the
-// per-state-dimension launch units.
+// per-state-dimension launch units (time-invariant: kf_n<N>_<precision>.cu;
+// time-varying models, kf_tv_*: kf_tv_n<N>.cu).
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
