@@ -8,6 +8,9 @@
 * oracle_cv_T64.npz: the oracle's own outputs on the 2D constant-velocity
   model (nx=4, ny=2, dt=0.1, q=1, R=0.25 I) at T=64, seed 1, a regression
   fixture that calls only oracle/.
+* oracle_tv_T48.npz: the same for a time-varying model (the seeded
+  ``tv_model(4, 48, seed=12)`` with inputs u, d, its arrays stored in the
+  fixture) at T = 48: filter, RTS, two-filter and the log-likelihood.
 """
 import json
 import math
@@ -37,6 +40,16 @@ def main():
     ms2, Ps2 = oracle.tf(model, y, mf, Pf)
     np.savez(os.path.join(HERE, "oracle_cv_T64.npz"), y=y, mf=mf, Pf=Pf, ms=ms, Ps=Ps, ms_tf=ms2,
              Ps_tf=Ps2, loglik=ll)
+    tv_fixture()
+
+
+def tv_fixture():
+    tv = W.tv_model(4, 48, seed=12)
+    y = W.simulate_tv(tv, seed=13)
+    ms, Ps, mf, Pf, ll = oracle.tv_smooth(tv, y, "rts")
+    ms2, Ps2 = oracle.tv_tf(tv, y, mf, Pf)
+    np.savez(os.path.join(HERE, "oracle_tv_T48.npz"), F=tv["F"], Q=tv["Q"], u=tv["u"], H=tv["H"], R=tv["R"],
+             d=tv["d"], m0=tv["m0"], P0=tv["P0"], y=y, mf=mf, Pf=Pf, ms=ms, Ps=Ps, ms_tf=ms2, Ps_tf=Ps2, loglik=ll)
 
 
 if __name__ == "__main__":

@@ -13,6 +13,9 @@ that do not come from the oracle:
   sequential Lemma 1 / Lemma 2 folds give the sequential recursions, and
   the reverse fold of (a_2, ..., a_T, e) gives the backward information
   filter (Alg. ptf).
+A stored fixture (tests/golden/oracle_tv_T48.npz, written by
+tests/golden/make_golden.py from the oracle alone) catches accidental
+changes.
 """
 import numpy as np
 import pytest
@@ -150,3 +153,16 @@ def test_tv_two_filter_reverse_fold_gives_backward_filter():
     for k in range(T - 1):
         assert rel(suf[k].eta, eta[k]) < 1e-10 and rel(suf[k].J, J[k]) < 1e-10
     assert np.all(suf[T - 1].eta == 0) and np.all(suf[T - 1].J == 0)
+
+
+def test_tv_oracle_regression_fixture():
+    """The stored outputs of tests/golden/make_golden.py for a time-varying
+    model (written by calling only the oracle) still match."""
+    import os
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "oracle_tv_T48.npz"))
+    model = {k: g[k] for k in ("F", "Q", "u", "H", "R", "d", "m0", "P0")}
+    ms, Ps, mf, Pf, ll = oracle.tv_smooth(model, g["y"], "rts")
+    ms2, Ps2 = oracle.tv_tf(model, g["y"], mf, Pf)
+    for a, b in ((mf, g["mf"]), (Pf, g["Pf"]), (ms, g["ms"]), (Ps, g["Ps"]), (ms2, g["ms_tf"]), (Ps2, g["Ps_tf"])):
+        assert rel(a, b) < 1e-13
+    assert abs(ll - float(g["loglik"])) < 1e-12 * abs(ll)
