@@ -14,10 +14,13 @@
  * Model (Sec. III-A, time-invariant, u = d = 0):
  *     x_k = F x_{k-1} + q_{k-1}, q ~ N(0,Q);  y_k = H x_k + r_k, r ~ N(0,R);
  *     x_0 ~ N(m0, P0), i.e. m0 = xbar_{0|0}, P0 = P_{0|0}.
+ * The kf_tv_* entry points take the general model with per-step matrices
+ * and inputs u, d instead (section "time-varying models" below).
  *
  * Conventions shared by every entry point
  *   - nx in {2, 4, 8}; 1 <= ny <= 8.  Other sizes return KF_ERR_ARG.
- *   - Model matrices are HOST pointers to row-major FP64 arrays owned by the
+ *   - Model matrices (kf_model_t; kf_tv_model_t holds per-step DEVICE arrays
+ *     instead) are HOST pointers to row-major FP64 arrays owned by the
  *     caller and copied during the call: F [nx][nx], Q [nx][nx] symmetric
  *     positive semi-definite, H [ny][nx], R [ny][ny] symmetric positive
  *     definite, m0 [nx], P0 [nx][nx] symmetric positive semi-definite.
@@ -159,6 +162,9 @@ kf_status_t kf_two_filter_smooth(const kf_model_t *model, int64_t T, const void 
  * positive semi-definite (and F_k P_{k|k} F_k^T + Q_k positive definite for
  * the RTS smoother); otherwise the outputs are not finite.
  * scan: KF_SCAN_AUTO or KF_SCAN_DECOUPLED_LOOKBACK (others: KF_ERR_ARG).
+ * The CTA size is fixed (128 threads) and the tuning table is not
+ * consulted; KF_OPT_WAIT_TIMEOUT_NS, KF_OPT_POSITIONS_PER_THREAD and
+ * KF_OPT_LOOKBACK_WARPS apply.
  * Workspace: kf_workspace_size(op, nx, ny, T, prec,
  * KF_SCAN_DECOUPLED_LOOKBACK) bytes, or NULL for the library's cache.
  * y, the outputs, loglik (innovation form with v_k = y_k - H_k xbar_{k|k-1}
