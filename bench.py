@@ -452,6 +452,54 @@ def workload_tv(args):
                       "results": res}))
 
 
+def cpu_baseline_jobs(jobs, what, seconds=10.0):
+    """The oracle (sequential FP64 C) over a list of jobs [(steps, fn)] on
+    every host core: one thread per core takes the next job in order until
+    `seconds` have passed (the oracle's ctypes calls release the GIL).
+    Steps/s over the jobs finished."""
+    import concurrent.futures as cf
+    import platform
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    lock = threading.Lock()
+    st = {"next": 0, "steps": 0, "jobs": 0}
+    t0 = time.perf_counter()
+
+    def worker():
+        while True:
+            with lock:
+                i = st["next"]
+                if i >= len(jobs) or time.perf_counter() - t0 > seconds:
+                    return
+                st["next"] = i + 1
+            steps, fn = jobs[i]
+            fn()
+            with lock:
+                st["steps"] += steps
+                st["jobs"] += 1
+
+    with cf.ThreadPoolExecutor(cores) as ex:
+        for f in [ex.submit(worker) for _ in range(cores)]:
+            f.result()
+    dt = time.perf_counter() - t0
+    return {"value": st["steps"] / dt, "unit": "smoothed steps/s", "cores": cores, "kind": "oracle",
+            "machine": platform.machine(),
+            "sample": "sequential FP64 C oracle, one thread per host core, %s: the first %d of %d jobs "
+                      "(%d steps), %.1f s" % (what, st["jobs"], len(jobs), st["steps"], dt)}
+
+
+def cpu_baseline_batch(model, y, offs, seconds=10.0):
+    """Kalman filter + RTS of the oracle over the batch's sequences, in order."""
+    import oracle
+    oracle.kf(model, y[:2])   # load the library once, before the threads
+
+    def job(i):
+        def fn():
+            mf, Pf, _ = oracle.kf(model, y[offs[i]:offs[i + 1]])
+            oracle.rts(model, mf, Pf)
+        return int(offs[i + 1] - offs[i]), fn
+    return cpu_baseline_jobs([job(i) for i in range(len(offs) - 1)], "Kalman filter + RTS per sequence", seconds)
+
+
 def workload_batch(args):
     """4096 tracking sequences, T log-uniform in [64, 65536], RTS smoother:
     one segmented scan over the whole batch vs one kf_rts_smooth call per
@@ -500,9 +548,10 @@ def workload_batch(args):
                      "one_launch_per_sequence": {"ms": float(done[-1]), "steps_per_s": total / (done[-1] * 1e-3),
                                                  "latency_p50_ms": float(np.percentile(done, 50)),
                                                  "latency_p99_ms": float(np.percentile(done, 99))}}
+    cpu = None if args.no_cpu_baseline else cpu_baseline_batch(model, y, offs)
     print(json.dumps({"workload": "batch", "metric": "smoothed steps/s", "unit": "smoothed steps/s",
                       "sequences": len(lengths), "total_steps": total,
-                      "lengths": "log-uniform in [64, 65536], seed 4", "results": res}))
+                      "lengths": "log-uniform in [64, 65536], seed 4", "results": res, "cpu_baseline": cpu}))
 
 
 def workload_serving(args):
@@ -587,6 +636,25 @@ def workload_serving(args):
         plain(i)
         plat.append(_t.perf_counter() - t0 - arrivals[i])
     t_plain = _t.perf_counter() - t0
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.kf(models[2], np.zeros((2, 1)))   # load the library once, before the threads
+
+        def cjob(i):
+            nx, T = int(nxs[i]), int(Ts[i])
+            mdl = models[nx]
+
+            def fn():
+                y = pools[nx][srcs[i], starts[i]:starts[i] + T].numpy().astype(np.float64)
+                mf, Pf, _ = oracle.kf(mdl, y)
+                if ops[i] == "rts":
+                    oracle.rts(mdl, mf, Pf)
+                elif ops[i] == "tf":
+                    oracle.tf(mdl, y, mf, Pf)
+            return T, fn
+        cpu = cpu_baseline_jobs([cjob(i) for i in range(n)], "the requests in arrival order (filter, RTS or "
+                                "two-filter as requested)")
     print(json.dumps({
         "workload": "serving", "metric": "smoothed steps/s", "unit": "smoothed steps/s",
         "requests": n, "rate_per_s": rate, "arrival_window_s": duration, "total_steps": steps,
@@ -596,7 +664,8 @@ def workload_serving(args):
                    "streams": 4},
         "one_call_per_request": {"steps_per_s": steps / t_plain, "wall_s": t_plain,
                                  "latency_p50_ms": 1e3 * float(np.median(plat)),
-                                 "latency_p99_ms": 1e3 * float(np.percentile(plat, 99))}}))
+                                 "latency_p99_ms": 1e3 * float(np.percentile(plat, 99))},
+        "cpu_baseline": cpu}))
 
 
 def main():
