@@ -217,6 +217,13 @@ kf_status_t kf_batch_smooth(kf_op_t op, const kf_model_t *models, int nmodels, c
                             int nseq, const int64_t *offsets, const void *y, kf_precision_t prec, void *m_out,
                             void *P_out, double *loglik, void *workspace, void *stream);
 
+/* kf_batch_smooth with op = KF_OP_RTS (Alg. prts on every sequence of the
+ * batch): smoothed means ms_out [total][nx] and covariances Ps_out
+ * [total][nx][nx]. */
+kf_status_t kf_batch_rts_smooth(const kf_model_t *models, int nmodels, const int32_t *model_of_seq, int nseq,
+                                const int64_t *offsets, const void *y, kf_precision_t prec, void *ms_out,
+                                void *Ps_out, double *loglik, void *workspace, void *stream);
+
 /* The batched call captured in a CUDA graph.  kf_batch_graph_create runs
  * kf_batch_smooth once with these arguments (writing the outputs) on a
  * private stream, with a workspace that the graph owns (cudaMalloc'd here),
@@ -310,6 +317,10 @@ kf_status_t kf_rts_smooth_noalloc(const kf_model_t *model, int64_t T, const void
  * out since the last call (its outputs are then undefined), or KF_ERR_CUDA
  * if the stream reported an error. */
 kf_status_t kf_sync_status(void *stream);
+
+/* The same as kf_sync_status(stream): the status of the kernels enqueued so
+ * far, read after `stream` has finished. */
+kf_status_t kf_stream_status(void *stream);
 
 /* Process-wide options read at the start of every later call.
  *   KF_OPT_WAIT_TIMEOUT_NS      bound of every inter-CTA wait in the

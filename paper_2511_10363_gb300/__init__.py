@@ -93,6 +93,10 @@ def lib():
             getattr(L, f).restype = ctypes.c_int
         L.kf_rts_smooth_noalloc.argtypes = [MP, i64, vp, i, vp, vp, vp, vp, vp]
         L.kf_batch_smooth.argtypes = [i, MP, i, vp, i, vp, vp, i, vp, vp, vp, vp, vp]
+        L.kf_batch_rts_smooth.argtypes = [MP, i, vp, i, vp, vp, i, vp, vp, vp, vp, vp]
+        L.kf_batch_rts_smooth.restype = ctypes.c_int
+        L.kf_stream_status.argtypes = [vp]
+        L.kf_stream_status.restype = ctypes.c_int
         L.kf_batch_smooth.restype = ctypes.c_int
         L.kf_batch_graph_create.argtypes = [i, MP, i, vp, i, vp, vp, i, vp, vp, vp, ctypes.POINTER(vp)]
         L.kf_batch_graph_launch.argtypes = [vp, vp]
@@ -332,6 +336,11 @@ def kf_sync_status(stream=None):
     return int(lib().kf_sync_status(_stream(stream)))
 
 
+def kf_stream_status(stream=None):
+    """The same as kf_sync_status."""
+    return int(lib().kf_stream_status(_stream(stream)))
+
+
 def kf_set_option(name, value):
     _check(lib().kf_set_option(OPTIONS[name], int(value)), "kf_set_option")
 
@@ -420,11 +429,7 @@ def kf_batch_workspace_size(op, nx, ny, total_steps, nseq, nmodels, precision="f
                                              PRECISIONS[precision], 1 if loglik else 0))
 
 
-def kf_batch_smooth(op, models, offsets, y, precision="fp32", model_of=None, m_out=None, P_out=None, loglik=False,
-                    workspace=None, stream=None):
-    """Batch of sequences concatenated in y [total, ny] (segmented scan).
-    models: one model dict (or Model) or a list; offsets: int64 array
-    [nseq + 1]; model_of: int32 array [nseq] or None.  Returns (m, P, ll)."""
+def _batch_args(models, offsets, y, precision, model_of, m_out, P_out, loglik):
     import torch
     if isinstance(models, (list, tuple)):
         ms = [_as_model(m) for m in models]
@@ -445,11 +450,33 @@ def kf_batch_smooth(op, models, offsets, y, precision="fp32", model_of=None, m_o
     if P_out is None:
         P_out = torch.empty((total, nx, nx), dtype=dt, device=y.device)
     ll = torch.empty(nseq, dtype=torch.float64, device=y.device) if loglik else None
+    return ms, arr, offs, nseq, mof, m_out, P_out, ll
+
+
+def kf_batch_smooth(op, models, offsets, y, precision="fp32", model_of=None, m_out=None, P_out=None, loglik=False,
+                    workspace=None, stream=None):
+    """Batch of sequences concatenated in y [total, ny] (segmented scan).
+    models: one model dict (or Model) or a list; offsets: int64 array
+    [nseq + 1]; model_of: int32 array [nseq] or None.  Returns (m, P, ll)."""
+    ms, arr, offs, nseq, mof, m_out, P_out, ll = _batch_args(models, offsets, y, precision, model_of, m_out, P_out,
+                                                             loglik)
     rc = lib().kf_batch_smooth(OPS[op], arr, len(ms), None if mof is None else mof.ctypes.data_as(ctypes.c_void_p),
                                nseq, offs.ctypes.data_as(ctypes.c_void_p), _ptr(y), PRECISIONS[precision],
                                _ptr(m_out), _ptr(P_out), _ptr(ll), _ptr(workspace), _stream(stream))
     _check(rc, "kf_batch_smooth")
     return m_out, P_out, ll
+
+
+def kf_batch_rts_smooth(models, offsets, y, precision="fp32", model_of=None, ms_out=None, Ps_out=None, loglik=False,
+                        workspace=None, stream=None):
+    """kf_batch_smooth with the RTS smoother.  Returns (ms, Ps, ll)."""
+    ms, arr, offs, nseq, mof, ms_out, Ps_out, ll = _batch_args(models, offsets, y, precision, model_of, ms_out,
+                                                               Ps_out, loglik)
+    rc = lib().kf_batch_rts_smooth(arr, len(ms), None if mof is None else mof.ctypes.data_as(ctypes.c_void_p), nseq,
+                                   offs.ctypes.data_as(ctypes.c_void_p), _ptr(y), PRECISIONS[precision],
+                                   _ptr(ms_out), _ptr(Ps_out), _ptr(ll), _ptr(workspace), _stream(stream))
+    _check(rc, "kf_batch_rts_smooth")
+    return ms_out, Ps_out, ll
 
 
 class BatchGraph:

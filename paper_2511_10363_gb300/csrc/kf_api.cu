@@ -944,6 +944,13 @@ kf_status_t kf_batch_smooth(kf_op_t op, const kf_model_t *models, int nmodels, c
                      stream);
 }
 
+kf_status_t kf_batch_rts_smooth(const kf_model_t *models, int nmodels, const int32_t *model_of_seq, int nseq,
+                                const int64_t *offsets, const void *y, kf_precision_t prec, void *ms_out,
+                                void *Ps_out, double *loglik, void *workspace, void *stream) {
+    return run_batch(KF_OP_RTS, models, nmodels, model_of_seq, nseq, offsets, y, prec, ms_out, Ps_out, loglik,
+                     workspace, stream);
+}
+
 // ---------------------------------------------------------------- batch graphs
 
 struct kf_batch_graph {
@@ -1173,6 +1180,8 @@ kf_status_t kf_sync_status(void *stream) {
     }
     return KF_OK;
 }
+
+kf_status_t kf_stream_status(void *stream) { return kf_sync_status(stream); }
 
 kf_status_t kf_trace_phases(kf_kernel_t kind, void *device_buffer, int capacity_tiles) {
     if (kind < 0 || kind > KF_KERNEL_TF_SCAN || capacity_tiles < 0) return KF_ERR_ARG;

@@ -190,3 +190,18 @@ def test_tv_argument_errors(lib):
         assert call_tv(m0=[0, np.nan, 0, 0], op=op) == 1
         assert call_tv(P0=-np.eye(4), op=op) == 2            # prior not PSD
         assert call_tv(P0=np.triu(np.ones((4, 4))), op=op) == 2   # not symmetric
+
+
+def test_batch_rts_smooth_argument_errors(lib):
+    mm = kf.Model(W.cv_model())
+    offs = np.array([0, 8, 16], dtype=np.int64)
+    L = kf.lib()
+
+    def call(nseq=2, offsets=offs, y=FAKE, m=FAKE, prec=1):
+        return L.kf_batch_rts_smooth(ctypes.byref(mm.c), 1, None, nseq, offsets.ctypes.data_as(ctypes.c_void_p), y,
+                                     prec, m, FAKE, None, None, None)
+    assert call(nseq=0) == 1
+    assert call(y=None) == 1
+    assert call(m=None) == 1
+    assert call(prec=7) == 1
+    assert call(offsets=np.array([0, 8, 4], dtype=np.int64)) == 1   # decreasing offsets
