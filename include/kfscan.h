@@ -294,16 +294,22 @@ kf_status_t kf_server_destroy(kf_server_t *srv);
  * cudaFree and no other allocating call, not even on its first use.
  *   - The caller still passes y, ms_out [T][nx] and Ps_out [T][nx][nx]
  *     (device, working precision), and may pass loglik (device double) and
- *     status_out (device int, may be NULL): status_out is set to 0 at the
+ *     status_out (device int, may be NULL).  status_out is set to 0 at the
  *     start of the call and receives KF_ERR_TIMEOUT if a bounded wait in a
- *     kernel runs out.
+ *     kernel runs out.  Without status_out the time-out goes to a status
+ *     word inside the array, which stays set until kf_sync_status (which
+ *     reads it beside the library's own word) reports and clears it; while
+ *     it is set, later calls without status_out give up their waits at once.
  *   - Its first call on a device looks up the device address of the array
  *     (cudaGetSymbolAddress); make that first call before capturing the
- *     stream into a graph.
+ *     stream into a graph.  The array is reserved when the library's device
+ *     code is loaded on that device -- under lazy module loading, at that
+ *     first call -- and a failure to reserve it there is returned as
+ *     KF_ERR_CUDA or KF_ERR_OOM.
  *   - Requests whose scratch would exceed the array (kf_workspace_size of an
- *     RTS call plus 256 bytes, i.e. about T <= 255,000 steps at nx = 4 in
- *     FP32) return KF_ERR_CAPACITY and enqueue nothing; kf_timing_enable
- *     must be off (KF_ERR_ARG otherwise).
+ *     RTS call plus 256 bytes, i.e. T <= 258,164 steps at nx = 4 in FP32)
+ *     return KF_ERR_CAPACITY and enqueue nothing; kf_timing_enable must be
+ *     off (KF_ERR_ARG otherwise).
  *   - All calls share the one array, which keeps the last call's contents;
  *     the call clears what must start at zero.  Calls whose work overlaps on
  *     the GPU (different streams, or different host threads) race on the

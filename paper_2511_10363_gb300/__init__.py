@@ -214,7 +214,10 @@ def _smooth(fn, name, model, y, precision, scan, ms_out, Ps_out, mf_out, Pf_out,
         ms_out = torch.empty((T, m.nx), dtype=dt, device=dev)
     if Ps_out is None:
         Ps_out = torch.empty((T, m.nx, m.nx), dtype=dt, device=dev)
-    ll = torch.empty(1, dtype=torch.float64, device=dev) if loglik else None
+    if isinstance(loglik, torch.Tensor):   # a caller's CUDA float64 [1] buffer
+        ll = loglik
+    else:
+        ll = torch.empty(1, dtype=torch.float64, device=dev) if loglik else None
     rc = fn(ctypes.byref(m.c), T, _ptr(y), PRECISIONS[precision], SCANS[scan], _ptr(ms_out), _ptr(Ps_out),
             _ptr(mf_out), _ptr(Pf_out), _ptr(ll), _ptr(workspace), _stream(stream))
     _check(rc, name)
@@ -310,7 +313,10 @@ def _tv_smooth(fn, name, model, y, precision, scan, ms_out, Ps_out, mf_out, Pf_o
         ms_out = torch.empty((T, m.nx), dtype=dt, device=dev)
     if Ps_out is None:
         Ps_out = torch.empty((T, m.nx, m.nx), dtype=dt, device=dev)
-    ll = torch.empty(1, dtype=torch.float64, device=dev) if loglik else None
+    if isinstance(loglik, torch.Tensor):   # a caller's CUDA float64 [1] buffer
+        ll = loglik
+    else:
+        ll = torch.empty(1, dtype=torch.float64, device=dev) if loglik else None
     rc = fn(ctypes.byref(m.c), T, _ptr(y), PRECISIONS[precision], SCANS[scan], _ptr(ms_out), _ptr(Ps_out),
             _ptr(mf_out), _ptr(Pf_out), _ptr(ll), _ptr(workspace), _stream(stream))
     _check(rc, name)

@@ -726,7 +726,8 @@ static kf_status_t noalloc_base(unsigned char **out) {
     if (!g_noalloc_base[dev]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return KF_ERR_CUDA;
+        if (e != cudaSuccess) return from_cuda(e);
+        if (!p) return KF_ERR_CUDA;
         g_noalloc_base[dev] = static_cast<unsigned char *>(p);
     }
     *out = g_noalloc_base[dev];
@@ -773,10 +774,24 @@ static kf_status_t rts_noalloc(const kf_model_t *md, int64_t T, const void *y, k
     q.no_lowrank = int(g_opt[KF_OPT_GENERAL_SOLVE].load());
     q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
     q.no_alloc = 1;
-    // the status word must start at zero (the scans' descriptors are cleared per launch)
-    cudaError_t e = cudaMemsetAsync(q.status, 0, sizeof(int), q.stream);
-    if (e != cudaSuccess) return from_cuda(e);
+    // A caller's status word starts at zero for this call.  Without one, the
+    // scratch word is sticky like the library's own status word: it is
+    // cleared only by kf_sync_status, which reads it too, so a time-out is
+    // never lost (the array is zero when the module loads).
+    if (status_out) {
+        cudaError_t e = cudaMemsetAsync(q.status, 0, sizeof(int), q.stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
     return from_cuda(launch_dispatch(q));
+}
+
+// The status word of kf_rts_smooth_noalloc calls made without status_out on
+// the current device (null before the first such lookup).
+static int *noalloc_status_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    return reinterpret_cast<int *>(g_noalloc_base[dev]);
 }
 }  // namespace kfs
 
@@ -1170,15 +1185,21 @@ kf_status_t kf_sync_status(void *stream) {
     int *p = nullptr;
     kf_status_t s = device_status_word(&p);
     if (s != KF_OK) return s;
-    int v = 0;
-    e = cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return KF_ERR_CUDA;
-    if (v != 0) {
-        e = cudaMemset(p, 0, sizeof(int));
+    // the library's word, then the no-allocation entry point's scratch word
+    int *words[2] = {p, noalloc_status_word()};
+    int first = 0;
+    for (int i = 0; i < 2; ++i) {
+        if (!words[i]) continue;
+        int v = 0;
+        e = cudaMemcpy(&v, words[i], sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return KF_ERR_CUDA;
-        return kf_status_t(v);
+        if (v != 0) {
+            e = cudaMemset(words[i], 0, sizeof(int));
+            if (e != cudaSuccess) return KF_ERR_CUDA;
+            if (!first) first = v;
+        }
     }
-    return KF_OK;
+    return kf_status_t(first);
 }
 
 kf_status_t kf_stream_status(void *stream) { return kf_sync_status(stream); }

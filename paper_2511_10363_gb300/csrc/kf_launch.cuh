@@ -562,12 +562,19 @@ static cudaError_t run_dlb(const typename P::Args &args, char *ws, size_t ctl_of
         ctl.sm_tab = smem;
         smem += P::tab_bytes();
     }
-    static int attr_smem = 0;   // dynamic shared memory already allowed for this instantiation
-    if (smem > attr_smem) {
-        cudaError_t e = cudaFuncSetAttribute(dlb_scan_kernel<P, THREADS, V, C>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_smem = smem;
+    {
+        // dynamic shared memory already allowed for this instantiation, per
+        // device (the attribute is a per-device setting)
+        static std::mutex mu;
+        static int attr_smem[64];
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lk(mu);
+        if (smem > attr_smem[dev]) {
+            cudaError_t e = cudaFuncSetAttribute(dlb_scan_kernel<P, THREADS, V, C>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            attr_smem[dev] = smem;
+        }
     }
     const TilePlan tp =
         plan_tiles(total, THREADS, THREADS * V, max_resident_tiles<P, THREADS, V, C>(dev, smem), q.k_override);

@@ -8,7 +8,14 @@ equal the elements of Eqs. pkf_init1..3 as the oracle writes them
 (K = Qe H^T S^{-1}, A = (I - K H) F, b = u + K (y - H u - d), ...), for
 (Qe, ue) = (Q_{k-1}, u_{k-1}) at k >= 2 and (P_{1|0}, xbar_{1|0}) at k = 1.
 At k = 1 only (A, b, C) are compared: eta_1 and J_1 never reach an output
-(A_1 = 0) and the two sides evaluate them with different S."""
+(A_1 = 0) and the two sides evaluate them with different S.
+
+This pins the algebra (a NumPy restatement of the formulas the device
+builders use), not the device code itself: tv_filter_elem and tv_rts_elem
+run only on the GPU, where tests/test_gpu_tv.py compares every filtered and
+smoothed moment with the time-varying oracle, including ny < nx (nx = 2, 4, 8
+with ny = 1, 2, 4, measurement rows padded to nx on the device) and non-zero
+inputs u and d, at FP64 within 1e-9."""
 import numpy as np
 import pytest
 

@@ -1,5 +1,5 @@
 """The no-allocation RTS smoother (kf_rts_smooth_noalloc) against the
-ordinary entry point.
+ordinary entry point and the FP64 oracle, and its wait time-out report.
 
 Some callers cannot allocate device memory during a call (their memory is
 owned by another allocator, or they cannot afford cudaMalloc's implicit
@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from tests.gpu_util import TOL, mean_err, cov_err
+from tests.gpu_util import TOL, mean_err, cov_err, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -58,3 +58,66 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
         kf.kf_rts_smooth_noalloc(model, y, "fp32", ms, Ps)
     assert e.value.status == 8       # KF_ERR_CAPACITY
     assert kf.kf_workspace_size("rts", 4, 2, T, "fp32", "dlb") + 256 > kf.NOALLOC_SCRATCH_BYTES
+
+
+def test_noalloc_matches_the_oracle():
+    """Against the FP64 oracle directly (not only against kf_rts_smooth), so a
+    mistake shared by both entry points cannot pass."""
+    import torch
+    import paper_2511_10363_gb300 as kf
+    model = W.cv_model()
+    T = 4097
+    y = W.simulate(model, T, seed=21)
+    ref = oracle_run(model, y)
+    yt = torch.tensor(y, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        ms = torch.full((T, 4), float("nan"), dtype=torch.float64, device="cuda")
+        Ps = torch.full((T, 4, 4), float("nan"), dtype=torch.float64, device="cuda")
+        ll = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        st = torch.full((1,), 77, dtype=torch.int32, device="cuda")
+        kf.kf_rts_smooth_noalloc(model, yt, "fp64", ms, Ps, loglik=ll, status_out=st)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        assert mean_err(ms.cpu().numpy(), ref["ms_rts"], ref["Ps_rts"]) <= 1e-9
+        assert cov_err(Ps.cpu().numpy(), ref["Ps_rts"]) <= 1e-9
+        assert abs(float(ll.item()) - ref["ll"]) <= 1e-9 * abs(ref["ll"])
+
+
+@pytest.mark.parametrize("with_status_out", [True, False])
+def test_noalloc_reports_a_wait_time_out(with_status_out):
+    """A tile that never publishes (test hook) makes the later tiles' bounded
+    waits run out.  The time-out reaches the caller's status word, or,
+    without one, kf_sync_status; the next call is correct."""
+    import torch
+    import paper_2511_10363_gb300 as kf
+    model = W.cv_model()
+    T = 20000
+    y = W.simulate(model, T, seed=9)
+    yt = torch.tensor(y, dtype=torch.float32, device="cuda")
+    ms = torch.empty((T, 4), dtype=torch.float32, device="cuda")
+    Ps = torch.empty((T, 4, 4), dtype=torch.float32, device="cuda")
+    st = torch.full((1,), 77, dtype=torch.int32, device="cuda") if with_status_out else None
+    assert kf.kf_sync_status() == 0
+    kf.kf_set_option("wait_timeout_ns", 50_000_000)
+    kf.kf_set_option("positions_per_thread", 2)
+    kf.kf_set_option("test_skip_tile", 3)
+    try:
+        kf.kf_rts_smooth_noalloc(model, yt, "fp32", ms, Ps, status_out=st)
+        torch.cuda.synchronize()
+    finally:
+        kf.kf_set_option("test_skip_tile", -1)
+        kf.kf_set_option("positions_per_thread", 0)
+        kf.kf_set_option("wait_timeout_ns", 10 ** 9)
+    if with_status_out:
+        assert int(st.item()) == 5               # KF_ERR_TIMEOUT
+        assert kf.kf_sync_status() == 0         # the library's word was not touched
+    else:
+        assert kf.kf_sync_status() == 5
+        assert kf.kf_sync_status() == 0         # read and cleared
+    ref = oracle_run(model, np.asarray(y, np.float32).astype(np.float64))
+    st2 = torch.full((1,), 77, dtype=torch.int32, device="cuda")
+    kf.kf_rts_smooth_noalloc(model, yt, "fp32", ms, Ps, status_out=st2)
+    torch.cuda.synchronize()
+    assert int(st2.item()) == 0
+    assert mean_err(ms.double().cpu().numpy(), ref["ms_rts"], ref["Ps_rts"]) <= TOL["fp32"]
+    assert cov_err(Ps.double().cpu().numpy(), ref["Ps_rts"]) <= TOL["fp32"]
