@@ -355,6 +355,15 @@ kf_status_t kf_stream_status(void *stream);
  *                               of two in 1 .. 2^30 (default 1, the paper's
  *                               "Sengupta A"; larger N, "Sengupta B", is
  *                               capped at the padded length).
+ *   KF_OPT_FILTER_KERNEL        0 (default): the forward filter scan of a
+ *                               time-invariant model with ny = nx / 2
+ *                               (nx 2 or 4, FP32 or FP64, one sequence, the
+ *                               decoupled look-back scan) runs the table
+ *                               kernel, whose data-independent coefficients
+ *                               (fold rows, run coefficients, the carry
+ *                               covariance at each tile's start) the host
+ *                               computes in FP64 and keeps in a device cache;
+ *                               1: the generic look-back kernel.
  * Returns KF_ERR_ARG for an unknown option or a value out of range. */
 typedef enum {
     KF_OPT_WAIT_TIMEOUT_NS = 0,
@@ -363,7 +372,8 @@ typedef enum {
     KF_OPT_THREADS = 3,
     KF_OPT_GENERAL_SOLVE = 4,
     KF_OPT_LOOKBACK_WARPS = 5,
-    KF_OPT_SENGUPTA_N = 6
+    KF_OPT_SENGUPTA_N = 6,
+    KF_OPT_FILTER_KERNEL = 7
 } kf_option_t;
 kf_status_t kf_set_option(kf_option_t opt, int64_t value);
 int64_t kf_get_option(kf_option_t opt); /* -1 for an unknown option */

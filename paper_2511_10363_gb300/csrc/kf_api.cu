@@ -234,7 +234,7 @@ static std::mutex g_mu;
 static void *g_ws[64];
 static size_t g_ws_bytes[64];
 static int *g_status[64];
-static std::atomic<int64_t> g_opt[8] = {1000000000LL, -1, 0, 0, 0, 0, 1, 0};
+static std::atomic<int64_t> g_opt[8] = {1000000000LL, -1, 0, 0, 0, 0, 1, 0};   // KF_OPT_* by index
 
 // KFSCAN_DEBUG=1 in the environment logs each stage of a call to stderr.
 bool debug_on() {
@@ -436,6 +436,99 @@ const void *scan_table_insert(uint64_t key, const void *host, size_t bytes, cuda
     return dst;
 }
 
+// ---- device cache of larger tables (time-invariant filter kernel)
+namespace {
+constexpr int BLOB_SLOTS = 8;
+struct BlobSlot {
+    uint64_t key, stamp;
+    size_t bytes;
+    char *ptr;
+    cudaEvent_t last_use;
+};
+struct BlobDev {
+    bool init = false, failed = false;
+    BlobSlot slot[BLOB_SLOTS];
+};
+std::mutex g_blob_mu;
+BlobDev g_blob[64];
+uint64_t g_blob_clock = 0;
+
+BlobDev *blob_dev(int *dev_out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    BlobDev &d = g_blob[dev];
+    if (d.failed) return nullptr;
+    if (!d.init) {
+        for (int i = 0; i < BLOB_SLOTS; ++i) {
+            d.slot[i].key = d.slot[i].stamp = 0;
+            d.slot[i].bytes = 0;
+            d.slot[i].ptr = nullptr;
+            if (cudaEventCreateWithFlags(&d.slot[i].last_use, cudaEventDisableTiming) != cudaSuccess) {
+                d.failed = true;
+                return nullptr;
+            }
+        }
+        d.init = true;
+    }
+    *dev_out = dev;
+    return &d;
+}
+}  // namespace
+
+const void *blob_lookup(uint64_t key, int *slot) {
+    std::lock_guard<std::mutex> lk(g_blob_mu);
+    int dev = 0;
+    BlobDev *d = blob_dev(&dev);
+    if (!d) return nullptr;
+    for (int i = 0; i < BLOB_SLOTS; ++i)
+        if (d->slot[i].ptr && d->slot[i].key == key) {
+            d->slot[i].stamp = ++g_blob_clock;
+            *slot = dev * BLOB_SLOTS + i;
+            return d->slot[i].ptr;
+        }
+    return nullptr;
+}
+
+const void *blob_insert(uint64_t key, const void *host, size_t bytes, cudaStream_t st, int *slot) {
+    std::lock_guard<std::mutex> lk(g_blob_mu);
+    int dev = 0;
+    BlobDev *d = blob_dev(&dev);
+    if (!d) return nullptr;
+    int v = 0;   // an empty slot, else the least recently used one
+    for (int i = 1; i < BLOB_SLOTS; ++i)
+        if (!d->slot[i].ptr || (d->slot[v].ptr && d->slot[i].stamp < d->slot[v].stamp)) v = i;
+    BlobSlot &b = d->slot[v];
+    if (b.ptr && b.bytes < bytes) {
+        if (cudaEventSynchronize(b.last_use) != cudaSuccess) return nullptr;
+        cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+    } else if (b.ptr && cudaEventSynchronize(b.last_use) != cudaSuccess) {
+        return nullptr;
+    }
+    if (!b.ptr) {
+        if (cudaMalloc(&b.ptr, bytes) != cudaSuccess) {
+            b.ptr = nullptr;
+            cudaGetLastError();
+            return nullptr;
+        }
+        b.bytes = bytes;
+    }
+    // pageable source: the copy has been staged when the call returns
+    if (cudaMemcpyAsync(b.ptr, host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return nullptr;
+    b.key = key;
+    b.stamp = ++g_blob_clock;
+    *slot = dev * BLOB_SLOTS + v;
+    return b.ptr;
+}
+
+void blob_used(int slot, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_blob_mu);
+    const int dev = slot / BLOB_SLOTS, i = slot % BLOB_SLOTS;
+    if (dev < 0 || dev >= 64 || !g_blob[dev].init) return;
+    cudaEventRecord(g_blob[dev].slot[i].last_use, st);
+}
+
 void scan_table_used(int slot, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_tsc_mu);
     const int dev = slot / TSC_SLOTS, i = slot % TSC_SLOTS;
@@ -555,6 +648,7 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
     q.no_lowrank = int(g_opt[KF_OPT_GENERAL_SOLVE].load());
     q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
     q.sg_n = g_opt[KF_OPT_SENGUPTA_N].load();
+    q.filter_kernel = int(g_opt[KF_OPT_FILTER_KERNEL].load());
     TuneCfg tc;
     if (scan == KF_SCAN_AUTO && tuned(op, md->nx, md->ny, q.prec, T, &tc)) {
         q.scan = tc.scan;
@@ -774,6 +868,7 @@ static kf_status_t rts_noalloc(const kf_model_t *md, int64_t T, const void *y, k
     q.no_lowrank = int(g_opt[KF_OPT_GENERAL_SOLVE].load());
     q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
     q.no_alloc = 1;
+    q.filter_kernel = 1;   // the table kernel keeps its tables in a device cache
     // A caller's status word starts at zero for this call.  Without one, the
     // scratch word is sticky like the library's own status word: it is
     // cleared only by kf_sync_status, which reads it too, so a time-out is
@@ -1243,8 +1338,9 @@ kf_status_t kf_measure_fma_peak(int fp64, double *flops_per_second) {
 }
 
 kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_SENGUPTA_N) return KF_ERR_ARG;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_FILTER_KERNEL) return KF_ERR_ARG;
     if (opt == KF_OPT_GENERAL_SOLVE && value != 0 && value != 1) return KF_ERR_ARG;
+    if (opt == KF_OPT_FILTER_KERNEL && value != 0 && value != 1) return KF_ERR_ARG;
     if (opt == KF_OPT_SENGUPTA_N && (value < 1 || value > (int64_t(1) << 30) || (value & (value - 1)) != 0))
         return KF_ERR_ARG;
     if (opt == KF_OPT_LOOKBACK_WARPS && (value < 0 || value > 32)) return KF_ERR_ARG;
@@ -1256,7 +1352,7 @@ kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
 }
 
 int64_t kf_get_option(kf_option_t opt) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_SENGUPTA_N) return -1;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_FILTER_KERNEL) return -1;
     return g_opt[opt].load();
 }
 

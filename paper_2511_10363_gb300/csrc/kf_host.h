@@ -59,6 +59,7 @@ struct LaunchReq {
     int no_alloc;        // the call may not allocate: no device table cache
     int64_t sg_n;        // Sengupta threshold N (power of two)
     int counters_zeroed; // the look-back counters of this pass were cleared already
+    int filter_kernel;   // 0: the time-invariant table kernel where it applies, 1: the generic scan kernel
 };
 
 // Device cache of tile-scan tables (kf_api.cu): a table is found by its key,
@@ -68,6 +69,13 @@ struct LaunchReq {
 const void *scan_table_lookup(uint64_t key, int *slot);
 const void *scan_table_insert(uint64_t key, const void *host, size_t bytes, cudaStream_t st, int *slot);
 void scan_table_used(int slot, cudaStream_t st);
+
+// Device cache of larger tables of any size (kf_api.cu), one allocation per
+// entry and a few entries per device, with the same find / insert / used
+// protocol.  Both return null when unavailable.
+const void *blob_lookup(uint64_t key, int *slot);
+const void *blob_insert(uint64_t key, const void *host, size_t bytes, cudaStream_t st, int *slot);
+void blob_used(int slot, cudaStream_t st);
 
 // A batch of sequences concatenated in y: sequence s covers
 // [offsets[s], offsets[s+1]) and uses model hms[model_of[s]].

@@ -748,12 +748,31 @@ static cudaError_t run_scan(const typename P::Args &args, char *ws, size_t ctl_o
 
 // ---------------------------------------------------------------- one operation
 
+// The forward filter scan on the time-invariant table kernel (ti_launch.cuh),
+// one translation unit per (nx, precision): false when the call does not
+// qualify, with nothing enqueued.
+bool ti_filter_launch(const FiltParams<2, float> &, const LaunchReq &, const KfBufs<float> &, char *,
+                      const WsLayout &, double *, cudaError_t *);
+bool ti_filter_launch(const FiltParams<4, float> &, const LaunchReq &, const KfBufs<float> &, char *,
+                      const WsLayout &, double *, cudaError_t *);
+bool ti_filter_launch(const FiltParams<2, double> &, const LaunchReq &, const KfBufs<double> &, char *,
+                      const WsLayout &, double *, cudaError_t *);
+bool ti_filter_launch(const FiltParams<4, double> &, const LaunchReq &, const KfBufs<double> &, char *,
+                      const WsLayout &, double *, cudaError_t *);
+
 // The forward pass with the general or the low-rank operator forms, through
 // the requested scan algorithm (DLB_ONLY: always the decoupled look-back scan).
 template <int N, typename R, int MODE, class Src, int THREADS, int V, bool DLB_ONLY>
 static cudaError_t filter_pass(const typename FilterFwd<N, R, MODE, Src>::Args &fa, bool lowrank, char *ws,
                                const WsLayout &L, const LaunchReq &q, double *ll) {
     constexpr int LRM = N / 2;
+    if constexpr (Src::ONE && N <= 4 && MODE == 0) {
+        // time-invariant model, one sequence: the table kernel
+        if (lowrank && q.filter_kernel == 0 && !q.no_alloc && (DLB_ONLY || q.scan == KF_SCAN_DLB_I)) {
+            cudaError_t e = cudaSuccess;
+            if (ti_filter_launch(fa.src.prm, q, fa.buf, ws, L, ll, &e)) return e;
+        }
+    }
     if (lowrank) {
         using PF = FilterFwd<N, R, MODE, Src, LRM>;
         typename PF::Args fl;

@@ -1,0 +1,11 @@
+// ti_n2_f32.cu -- the time-invariant forward filter table kernel, nx = 2, FP32.
+#include "ti_launch.cuh"
+
+namespace kfs {
+
+bool ti_filter_launch(const FiltParams<2, float> &prm, const LaunchReq &q, const KfBufs<float> &buf, char *ws,
+                      const WsLayout &L, double *ll, cudaError_t *err) {
+    return ti_filter_launch_impl<2, float>(prm, q, buf, ws, L, ll, err);
+}
+
+}  // namespace kfs
