@@ -9,11 +9,12 @@
 //   3. a warp Kogge-Stone scan (shuffles) and a scan of the warp aggregates
 //      give every thread its exclusive prefix inside the tile and the tile
 //      aggregate, which is published (flag 1);
-//   4. look-back: every thread takes V predecessor tiles, waits (bounded)
-//      until each has published, and the CTA finds the nearest predecessor
-//      that already published its inclusive prefix (flag 2); the aggregates
-//      after it are reduced in order by the whole CTA (thread folds, warp
-//      shuffle tree, warp-0 tree) and applied to that inclusive carry;
+//   4. look-back: one warp waits (bounded, with back-off) until the
+//      predecessors after the nearest one that already published its
+//      inclusive prefix (flag 2) have published their aggregates; the
+//      aggregates after it are reduced in order by the look-back warps
+//      (thread folds, warp shuffle tree, warp-0 tree) and applied to that
+//      inclusive carry;
 //   5. the tile's inclusive carry is published (flag 2);
 //   6. each thread walks its K elements again, extending the carry one
 //      element at a time with the one-sided operator, and emits its outputs
@@ -59,11 +60,6 @@ struct DlbCtl {
 
 constexpr int KF_STATUS_TIMEOUT = 5;
 
-KF_D int ld_acquire(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 KF_D void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -76,24 +72,6 @@ KF_D uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
-}
-
-// Wait until *f != 0; returns the flag, or 0 when the wait ran out or
-// another CTA already failed.
-KF_D int wait_flag(const int *f, const DlbCtl &ctl) {
-    int v = ld_acquire(f);
-    if (v) return v;
-    const uint64_t t0 = global_ns();
-    for (;;) {
-        __nanosleep(64);
-        v = ld_acquire(f);
-        if (v) return v;
-        if (ld_relaxed(ctl.status) != 0) return 0;
-        if (int64_t(global_ns() - t0) > ctl.timeout_ns) {
-            atomicCAS(ctl.status, 0, KF_STATUS_TIMEOUT);
-            return 0;
-        }
-    }
 }
 
 template <class X>
@@ -445,35 +423,49 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
         const int lbt = 32 * ctl.lbw;
         const int vv = (ctl.ntiles + lbt - 1) / lbt;
         const bool lbthread = tid < lbt;
-        int qloc = -1;
-        if (lbthread) {
-            // all of this thread's flags are read at once (relaxed, in flight
-            // together); only the ones not yet set are then waited for, and
-            // one acquire fence orders the flags before the aggregate loads
-            // (vv <= 32: at most 1024 tiles over at least 32 threads)
-            unsigned pend = 0;
-#pragma unroll 1
-            for (int v = 0; v < vv; ++v) {
-                const int q = tile - 1 - (tid * vv + v);
-                if (q >= 0) {
-                    const int f = ld_relaxed(ctl.flags + q);
-                    if (f == 0) pend |= 1u << v;
-                    else if (f == 2 && q > qloc) qloc = q;
+        // One warp (the last) waits until every predecessor has published:
+        // its lanes read the flags together, back off exponentially between
+        // rounds (so the waiting tiles leave the L2 to the tiles still
+        // working) and find the nearest predecessor with an inclusive prefix;
+        // the rest of the CTA waits at the barrier.
+        if (warp == NW - 1) {
+            bool ok = true;
+            int qloc = -1;
+            for (int q0 = tile - 1; q0 >= 0 && ok; q0 -= 32) {
+                const int q = q0 - lane;
+                int f = q >= 0 ? ld_relaxed(ctl.flags + q) : 1;
+                unsigned ns = 32;
+                const uint64_t t0 = global_ns();
+                while (!__all_sync(0xffffffffu, f != 0)) {
+                    __nanosleep(ns);
+                    ns = ns < 1024 ? 2 * ns : 1024;
+                    if (f == 0) f = ld_relaxed(ctl.flags + q);
+                    const bool fail = ld_relaxed(ctl.status) != 0 || int64_t(global_ns() - t0) > ctl.timeout_ns;
+                    if (__any_sync(0xffffffffu, fail)) {
+                        if (lane == 0) atomicCAS(ctl.status, 0, KF_STATUS_TIMEOUT);
+                        ok = false;
+                        break;
+                    }
                 }
+                if (q >= 0 && f == 2 && q > qloc) qloc = q;
+                // the nearest inclusive prefix ends the search
+                if (__any_sync(0xffffffffu, q >= 0 && f == 2)) break;
             }
-#pragma unroll 1
-            for (int v = 0; v < vv; ++v) {
-                if (!((pend >> v) & 1u)) continue;
-                const int q = tile - 1 - (tid * vv + v);
-                const int f = wait_flag(ctl.flags + q, ctl);
-                if (f == 0) s_abort = 1;
-                if (f == 2 && q > qloc) qloc = q;
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                const int o = __shfl_down_sync(0xffffffffu, qloc, s);
+                qloc = o > qloc ? o : qloc;
             }
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+            if (lane == 0) {
+                s_qstar = qloc;
+                if (!ok) s_abort = 1;
+            }
         }
-        if (qloc >= 0) atomicMax(&s_qstar, qloc);
         __syncthreads();
         if (s_abort) return;
+        // the flags were read by another warp: the barrier and an acquire
+        // fence order them before the loads of the published aggregates
+        if (lbthread) asm volatile("fence.acq_rel.gpu;" ::: "memory");
         if (trace) trace[5] = global_ns();
         const int qstar = s_qstar;
         if (lbthread) {

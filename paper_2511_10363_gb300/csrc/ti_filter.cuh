@@ -29,8 +29,9 @@
 //   6. every thread applies its warp's and its own exclusive run to the tile
 //      carry (one-sided Lemma 1 in the Cholesky form of apply_run_chol), then
 //      walks its K elements with the rank-ny carry update (apply_fwd_lr_parts),
-//      writes the filter records through shared memory with bulk
-//      asynchronous copies, and adds its log-likelihood terms.
+//      and adds its log-likelihood terms; each warp writes the filter records
+//      of its 32 runs chunk by chunk through shared memory, as coalesced
+//      16-byte stores (per run, the records of a chunk are contiguous).
 // Every wait is bounded by a wall-clock limit; on time-out the CTA records
 // the time-out in the status word and returns.
 #pragma once
@@ -46,12 +47,14 @@ struct TiTab {
     static constexpr int M = N / 2, NN = N * N, S = N * (N + 1) / 2;
     static constexpr int E = NN + 2 * N * M;    // fold row: T1 | T4 | T3U
     static constexpr int WE = 4 * NN;           // coefficient set: M1 | M2 | M3 | M4
-    static constexpr int WES = WE + 1;          // its stride in shared memory (odd: no bank conflicts)
+    static constexpr int Q = 16 / int(sizeof(R));
+    static constexpr int WES = WE + Q;          // its stride in shared memory: an odd number of
+                                                // 16-byte units, so 16-byte loads of distinct sets
+                                                // by the lanes of a quarter warp hit distinct banks
     static constexpr int NSETS = 31 + 7;        // warp level (s, p), then warp-aggregate level
     static constexpr int PE = NN + 2 * S;       // run of c thread aggregates: A | C | J (packed)
     static constexpr int NSPAN = 40;            // c = 0 .. 32, then 32 w for w = 2 .. 8
     static constexpr int TE = 2 * S + 2 * NN;   // tile: C_{i-1} | chol(C_{i-1}) | X_i | Y_i
-    static constexpr int Q = 16 / int(sizeof(R));
     static constexpr int TES = (TE + Q - 1) / Q * Q;
     static constexpr int UP = (N + Q - 1) / Q * Q;   // published u_i, padded to 16 bytes
     static KF_HD int wset(int s, int p) { return s + p - 2; }
@@ -82,23 +85,8 @@ struct TiArgs {
     int trace_cap;
 };
 
-// ---------------------------------------------------------------- bulk asynchronous copies
+// ---------------------------------------------------------------- flags
 
-KF_D void ti_fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-KF_D void ti_bulk_store(void *gdst, const void *ssrc, unsigned bytes) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(ssrc));
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(s), "r"(bytes)
-                 : "memory");
-}
-KF_D void ti_bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-KF_D void ti_bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-KF_D void ti_bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-KF_D int ti_ld_acquire(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 KF_D int ti_ld_relaxed(const int *p) {
     int v;
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -109,23 +97,6 @@ KF_D uint64_t ti_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
-}
-
-// Bounded wait for *f != 0: false when it ran out (the time-out is then in
-// the status word) or another CTA already failed.
-template <int N, typename R>
-KF_D bool ti_wait(const int *f, const TiArgs<N, R> &a) {
-    if (ti_ld_acquire(f)) return true;
-    const uint64_t t0 = ti_ns();
-    for (;;) {
-        __nanosleep(64);
-        if (ti_ld_acquire(f)) return true;
-        if (ti_ld_relaxed(a.status) != 0) return false;
-        if (int64_t(ti_ns() - t0) > a.timeout_ns) {
-            atomicCAS(a.status, 0, 5);   // KF_ERR_TIMEOUT
-            return false;
-        }
-    }
 }
 
 // ---------------------------------------------------------------- small dense helpers
@@ -248,18 +219,24 @@ KF_D void apply_run_chol(const R *L, const R *Ldinv, const R *b, const R *A, con
     }
 }
 
-// (b, eta) <- (bx, ex) (x) (b, eta) with the coefficient set w (shared memory).
+// (b, eta) <- (bx, ex) (x) (b, eta) with the coefficient set w (shared
+// memory, 16-byte aligned), read row by row as vectors.
 template <int N, typename R>
 KF_D void ti_combine(const R *w, const R *bx, const R *ex, R *b, R *e) {
     constexpr int NN = N * N;
     R nb[N], ne[N];
 #pragma unroll
     for (int r = 0; r < N; ++r) {
+        R m1[N], m2[N], m3[N], m4[N];
+        load_rec<N>(m1, w + r * N);
+        load_rec<N>(m2, w + NN + r * N);
+        load_rec<N>(m3, w + 2 * NN + r * N);
+        load_rec<N>(m4, w + 3 * NN + r * N);
         R sb = b[r], se = ex[r];
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            sb += w[r * N + k] * bx[k] + w[NN + r * N + k] * e[k];
-            se += w[2 * NN + r * N + k] * e[k] - w[3 * NN + r * N + k] * bx[k];
+            sb += m1[k] * bx[k] + m2[k] * e[k];
+            se += m3[k] * e[k] - m4[k] * bx[k];
         }
         nb[r] = sb;
         ne[r] = se;
@@ -310,8 +287,17 @@ KF_D void ti_emit(const TiArgs<N, R> &a, int64_t g, const R *b, const R *C, R *s
     }
 }
 
-// Threads per CTA THREADS, records per staged chunk CH (two chunks per
-// thread in flight), MINB resident CTAs per SM.
+// Shared-memory bytes of the record staging of one CTA: per warp, the next
+// CH records of its 32 runs, each run's chunk at an odd number of 16-byte
+// units so that the lanes' record stores hit distinct banks.
+template <int N, typename R, int THREADS, int CH>
+KF_HD constexpr int ti_stage_bytes() {
+    constexpr int FB = FRec<N, R>::SIZE * int(sizeof(R));
+    return (THREADS / 32) * 32 * (((CH * FB / 16) | 1) * 16);
+}
+
+// Threads per CTA THREADS, records per staged chunk CH, MINB resident CTAs
+// per SM.
 template <int N, typename R, int THREADS, int CH, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_constant__ TiArgs<N, R> a) {
     using TT = TiTab<N, R>;
@@ -323,18 +309,21 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
     __shared__ R s_tb[N];                    // the tile's carry mean
     __shared__ double s_ll[NW];
     __shared__ int s_tile, s_abort, s_last;
+    __shared__ unsigned long long s_twait;   // phase trace: the last look-back wait to end
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     extern __shared__ __align__(16) unsigned char dsm[];
     R *const rows = reinterpret_cast<R *>(dsm);
     R *const sets = rows + TT::al((a.K > 1 ? a.K - 1 : 0) * E);
     unsigned char *const stage = reinterpret_cast<unsigned char *>(sets + TT::al(TT::NSETS * TT::WES));
-    constexpr int STB = 2 * CH * FR * int(sizeof(R)) + 16;   // bytes of one thread's staging ring
-    R *const mystage = a.frec ? reinterpret_cast<R *>(stage + tid * STB) : nullptr;
+    constexpr int RU = FR * int(sizeof(R)) / 16;              // 16-byte units of a record,
+    constexpr int SEGU = CH * RU, STRU = SEGU | 1;            // of a run's chunk, and its odd stride
+    float4 *const wstage = a.frec ? reinterpret_cast<float4 *>(stage) + warp * 32 * STRU : nullptr;
 
     if (tid == 0) {
         s_tile = atomicAdd(a.counters, 1);
         s_abort = 0;
+        s_twait = 0;
     }
     // tables into shared memory
     {
@@ -503,6 +492,34 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
 
     // ---- 5. look-back: b_{i-1} = the maps of tiles 0 .. i-1 composed in order
     if (tile > 0) {
+        // one warp (the last, idle while warp 0 publishes) waits until every
+        // preceding tile has published: its lanes read the flags together and
+        // back off exponentially between rounds, so that the waiting tiles
+        // keep the L2 free for the tiles still working; the rest of the CTA
+        // waits at the barrier
+        if (warp == NW - 1) {
+            bool ok = true;
+            for (int q0 = 0; q0 < tile && ok; q0 += 32) {
+                const int q = q0 + lane;
+                bool seen = q >= tile || ti_ld_relaxed(a.flags + q) != 0;
+                unsigned ns = 32;
+                const uint64_t t0 = ti_ns();
+                while (!__all_sync(0xffffffffu, seen)) {
+                    __nanosleep(ns);
+                    ns = ns < 1024 ? 2 * ns : 1024;
+                    if (!seen) seen = ti_ld_relaxed(a.flags + q) != 0;
+                    const bool fail = ti_ld_relaxed(a.status) != 0 || int64_t(ti_ns() - t0) > a.timeout_ns;
+                    if (__any_sync(0xffffffffu, fail)) {
+                        if (lane == 0) atomicCAS(a.status, 0, 5);   // KF_ERR_TIMEOUT (kept if already set)
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+            if (!ok && lane == 0) s_abort = 1;
+        }
+        __syncthreads();
+        if (s_abort) return;
         const int lbt = 32 * a.lbw;
         const int vv = (tile + lbt - 1) / lbt;
         if (tid < lbt) {
@@ -512,12 +529,12 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
             for (int i = 0; i < NN; ++i) F[i] = (i % (N + 1) == 0) ? R(1) : R(0);
 #pragma unroll
             for (int i = 0; i < N; ++i) v[i] = 0;
+            // the flags were seen by another thread of the CTA: the barrier and
+            // an acquire fence order them before the loads of the published maps
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+            const int q0 = tid * vv, q1 = (q0 + vv < tile) ? q0 + vv : tile;
 #pragma unroll 1
-            for (int q = tid * vv; q < tid * vv + vv && q < tile; ++q) {
-                if (!ti_wait(a.flags + q, a)) {
-                    s_abort = 1;
-                    break;
-                }
+            for (int q = q0; q < q1; ++q) {
                 const R *X = a.tab + a.off_tiles + int64_t(q) * TT::TES + 2 * S;
                 R Xq[NN], uq[TT::UP];
 #pragma unroll
@@ -555,6 +572,7 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
                     for (int i = 0; i < N; ++i) v[i] = nv[i];
                 }
             }
+            if (a.trace) atomicMax(&s_twait, (unsigned long long)ti_ns());
             // lanes hold consecutive blocks of tiles, earliest first: compose
             // the later block over the earlier one, down to lane 0
 #pragma unroll 1
@@ -586,6 +604,8 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
                     for (int i = 0; i < N; ++i) v[i] = nv[i];
                 }
             }
+            if (lane == 0 && a.trace && tile < a.trace_cap && warp < 6)
+                a.trace[16 * tile + 8 + warp] = ti_ns();   // phase trace: warp w's tree done
             if (lane == 0) {
 #pragma unroll
                 for (int i = 0; i < NN; ++i) s_lx[warp][i] = F[i];
@@ -593,8 +613,10 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
                 for (int i = 0; i < N; ++i) s_lx[warp][NN + i] = v[i];
             }
         }
+        if (trace) trace[7] = ti_ns();
         __syncthreads();
-        if (s_abort) return;
+        if (trace) trace[6] = s_twait;
+        if (trace) trace[14] = ti_ns();
         if (tid == 0) {   // warps in order: only the mean of the composition is needed
             R v[N];
 #pragma unroll
@@ -613,6 +635,7 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
             }
 #pragma unroll
             for (int i = 0; i < N; ++i) s_tb[i] = v[i];
+            if (trace) trace[15] = ti_ns();
         }
     } else if (tid == 0) {   // tile 0: the carry is s_1 = (b_1, P_{1|1})
         R y1[M];
@@ -706,14 +729,14 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
         }
     }
     {
-        const int64_t n = r1 > r0 ? r1 - r0 : 0;
-        const int nch = int((n + CH - 1) / CH);
+        // chunks of CH steps, the same count for every lane of the warp (the
+        // lanes share each chunk's store)
+        const int nch = (a.K + CH - 1) / CH;
 #pragma unroll 1
         for (int ch = 0; ch < nch; ++ch) {
-            R *buf = mystage ? mystage + (ch & 1) * CH * FR : nullptr;
-            if (buf) ti_bulk_wait_read1();   // the copy that last read this buffer is done
+            R *buf = wstage ? reinterpret_cast<R *>(wstage + lane * STRU) : nullptr;
             const int64_t p0 = r0 + int64_t(ch) * CH;
-            const int cnt = int(r1 - p0 < CH ? r1 - p0 : CH);
+            const int cnt = int(r1 - p0 < CH ? (r1 - p0 > 0 ? r1 - p0 : 0) : CH);
             R llc = 0;
 #pragma unroll
             for (int cc = 0; cc < CH; ++cc) {
@@ -740,13 +763,21 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
                 ti_emit<N, R>(a, g, c.v + FwdCarry<N, R>::ob, c.v + FwdCarry<N, R>::oC, buf ? buf + cc * FR : nullptr);
             }
             ll += double(llc);
-            if (buf) {
-                ti_fence_async_smem();
-                ti_bulk_store(a.frec + (p0 + 1) * FR, buf, unsigned(cnt * FR * int(sizeof(R))));
-                ti_bulk_commit();
+            if (wstage) {   // the warp's 32 chunks, each run's records contiguous in memory
+                __syncwarp();
+                float4 *g = reinterpret_cast<float4 *>(a.frec);
+                const int64_t wr0 = (int64_t(tile) * THREADS + warp * 32) * a.K;   // lane 0's first position
+#pragma unroll 2
+                for (int idx = lane; idx < 32 * SEGU; idx += 32) {
+                    const int run = idx / SEGU, o = idx - run * SEGU;
+                    const int64_t rs = wr0 + int64_t(run) * a.K;               // the run's first position
+                    const int64_t re = rs + a.K < treg ? rs + a.K : treg;      // one past its last
+                    const int64_t pos = rs + int64_t(ch) * CH + o / RU;
+                    if (pos < re) g[(pos + 1) * RU + o % RU] = wstage[run * STRU + o];
+                }
+                __syncwarp();
             }
         }
-        if (mystage) ti_bulk_wait_all();
     }
     if (trace) trace[5] = ti_ns();
 

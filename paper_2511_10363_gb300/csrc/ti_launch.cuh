@@ -144,10 +144,10 @@ struct TiCfg {
     static constexpr int CH = (sizeof(R) == 8 && THREADS == 256) ? 1 : 2;
     static constexpr int MINB = THREADS == 256 ? 2 : 4;
     static constexpr int KT = FoldTab<N, N / 2, R>::KT;   // fold rows at most
-    static constexpr int STB = 2 * CH * FRec<N, R>::SIZE * int(sizeof(R)) + 16;
     static int smem(bool staged) {
         using TT = TiTab<N, R>;
-        return int(sizeof(R)) * (TT::al(KT * TT::E) + TT::al(TT::NSETS * TT::WES)) + (staged ? THREADS * STB : 0);
+        return int(sizeof(R)) * (TT::al(KT * TT::E) + TT::al(TT::NSETS * TT::WES)) +
+               (staged ? ti_stage_bytes<N, R, THREADS, CH>() : 0);
     }
 };
 
@@ -162,7 +162,9 @@ static int ti_resident(int dev, bool staged) {
     if (v == 0) {
         auto kern = ti_filter_kernel<N, R, THREADS, CF::CH, CF::MINB>;
         const int smem = CF::smem(staged);
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+        // the attribute allows the larger (staged) size, whichever launch comes first
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::smem(true)) != cudaSuccess)
+            return 0;
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, THREADS, smem) != cudaSuccess || per < 1) return 0;

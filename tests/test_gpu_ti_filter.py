@@ -69,8 +69,8 @@ def test_table_kernel_against_oracle(precision, nx, threads, T, K):
 @pytest.mark.parametrize("op", ["rts", "tf"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_table_kernel_feeds_the_smoothers(op, precision):
-    """The filter records the table kernel writes (bulk asynchronous copies
-    from shared memory) are what the smoother passes read."""
+    """The filter records the table kernel writes (staged per warp in shared
+    memory, coalesced stores) are what the smoother passes read."""
     model, y, out = run_case(op, 4, 30001, precision, 256, 0, seed=5, loglik=(precision == "fp64"))
     ref = oracle_run(model, y)
     key = "rts" if op == "rts" else "tf"
@@ -115,3 +115,16 @@ def test_table_kernel_wait_times_out_and_recovers():
     out = gpu_run("filter", model, y, "fp64", "dlb", loglik=True)
     ref = oracle_run(model, y)
     assert mean_err(out["mf"], ref["mf"], ref["Pf"]) < 1e-9 and cov_err(out["Pf"], ref["Pf"]) < 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("threads", [128, 256])
+def test_plain_and_smoother_launches_interleave(precision, threads):
+    """A plain filter call (no record staging, less shared memory) between
+    smoother calls (records staged) of the same kernel configuration: every
+    launch must be allowed its shared memory, whichever ran first."""
+    for op in ("rts", "filter", "rts", "filter"):
+        model, y, out = run_case(op, 4, 3000, precision, threads, 0, seed=31, loglik=False)
+        ref = oracle_run(model, y)
+        tol = TOL[precision]
+        assert mean_err(out["mf"], ref["mf"], ref["Pf"]) <= tol and cov_err(out["Pf"], ref["Pf"]) <= tol
