@@ -364,6 +364,10 @@ kf_status_t kf_stream_status(void *stream);
  *                               covariance at each tile's start) the host
  *                               computes in FP64 and keeps in a device cache;
  *                               1: the generic look-back kernel.
+ *   KF_OPT_RTS_KERNEL           0 (default): the RTS smoother pass of one
+ *                               sequence (nx 2 or 4, the decoupled look-back
+ *                               scan) runs its dedicated kernel; 1: the
+ *                               generic look-back kernel.
  * Returns KF_ERR_ARG for an unknown option or a value out of range. */
 typedef enum {
     KF_OPT_WAIT_TIMEOUT_NS = 0,
@@ -373,7 +377,8 @@ typedef enum {
     KF_OPT_GENERAL_SOLVE = 4,
     KF_OPT_LOOKBACK_WARPS = 5,
     KF_OPT_SENGUPTA_N = 6,
-    KF_OPT_FILTER_KERNEL = 7
+    KF_OPT_FILTER_KERNEL = 7,
+    KF_OPT_RTS_KERNEL = 8
 } kf_option_t;
 kf_status_t kf_set_option(kf_option_t opt, int64_t value);
 int64_t kf_get_option(kf_option_t opt); /* -1 for an unknown option */

@@ -31,7 +31,8 @@ OPS = {"filter": 0, "rts": 1, "two_filter": 2, "tf": 2}
 STATUS = {0: "KF_OK", 1: "KF_ERR_ARG", 2: "KF_ERR_NOT_PD", 3: "KF_ERR_CUDA", 4: "KF_ERR_OOM",
           5: "KF_ERR_TIMEOUT", 6: "KF_ERR_BUDGET", 7: "KF_ERR_BUSY", 8: "KF_ERR_CAPACITY"}
 OPTIONS = {"wait_timeout_ns": 0, "test_skip_tile": 1, "positions_per_thread": 2, "threads": 3, "general_solve": 4,
-           "lookback_warps": 5, "sengupta_n": 6, "filter_kernel": 7}
+           "lookback_warps": 5, "sengupta_n": 6, "filter_kernel": 7,
+           "rts_kernel": 8}
 
 _lib = None
 

@@ -234,7 +234,7 @@ static std::mutex g_mu;
 static void *g_ws[64];
 static size_t g_ws_bytes[64];
 static int *g_status[64];
-static std::atomic<int64_t> g_opt[8] = {1000000000LL, -1, 0, 0, 0, 0, 1, 0};   // KF_OPT_* by index
+static std::atomic<int64_t> g_opt[9] = {1000000000LL, -1, 0, 0, 0, 0, 1, 0, 0};   // KF_OPT_* by index
 
 // KFSCAN_DEBUG=1 in the environment logs each stage of a call to stderr.
 bool debug_on() {
@@ -649,6 +649,7 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
     q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
     q.sg_n = g_opt[KF_OPT_SENGUPTA_N].load();
     q.filter_kernel = int(g_opt[KF_OPT_FILTER_KERNEL].load());
+    q.rts_kernel = int(g_opt[KF_OPT_RTS_KERNEL].load());
     TuneCfg tc;
     if (scan == KF_SCAN_AUTO && tuned(op, md->nx, md->ny, q.prec, T, &tc)) {
         q.scan = tc.scan;
@@ -869,6 +870,7 @@ static kf_status_t rts_noalloc(const kf_model_t *md, int64_t T, const void *y, k
     q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
     q.no_alloc = 1;
     q.filter_kernel = 1;   // the table kernel keeps its tables in a device cache
+    q.rts_kernel = 1;      // the kernels of this entry point stay as they were when it was added
     // A caller's status word starts at zero for this call.  Without one, the
     // scratch word is sticky like the library's own status word: it is
     // cleared only by kf_sync_status, which reads it too, so a time-out is
@@ -1338,9 +1340,9 @@ kf_status_t kf_measure_fma_peak(int fp64, double *flops_per_second) {
 }
 
 kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_FILTER_KERNEL) return KF_ERR_ARG;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_RTS_KERNEL) return KF_ERR_ARG;
     if (opt == KF_OPT_GENERAL_SOLVE && value != 0 && value != 1) return KF_ERR_ARG;
-    if (opt == KF_OPT_FILTER_KERNEL && value != 0 && value != 1) return KF_ERR_ARG;
+    if ((opt == KF_OPT_FILTER_KERNEL || opt == KF_OPT_RTS_KERNEL) && value != 0 && value != 1) return KF_ERR_ARG;
     if (opt == KF_OPT_SENGUPTA_N && (value < 1 || value > (int64_t(1) << 30) || (value & (value - 1)) != 0))
         return KF_ERR_ARG;
     if (opt == KF_OPT_LOOKBACK_WARPS && (value < 0 || value > 32)) return KF_ERR_ARG;
@@ -1352,7 +1354,7 @@ kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
 }
 
 int64_t kf_get_option(kf_option_t opt) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_FILTER_KERNEL) return -1;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_RTS_KERNEL) return -1;
     return g_opt[opt].load();
 }
 

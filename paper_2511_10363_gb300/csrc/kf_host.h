@@ -60,6 +60,7 @@ struct LaunchReq {
     int64_t sg_n;        // Sengupta threshold N (power of two)
     int counters_zeroed; // the look-back counters of this pass were cleared already
     int filter_kernel;   // 0: the time-invariant table kernel where it applies, 1: the generic scan kernel
+    int rts_kernel;      // 0: the dedicated one-sequence RTS kernel where it applies, 1: the generic scan kernel
 };
 
 // Device cache of tile-scan tables (kf_api.cu): a table is found by its key,

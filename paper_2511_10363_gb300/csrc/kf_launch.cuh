@@ -759,6 +759,16 @@ bool ti_filter_launch(const FiltParams<2, double> &, const LaunchReq &, const Kf
                       const WsLayout &, double *, cudaError_t *);
 bool ti_filter_launch(const FiltParams<4, double> &, const LaunchReq &, const KfBufs<double> &, char *,
                       const WsLayout &, double *, cudaError_t *);
+// The RTS pass of one sequence on its dedicated kernel (rts_launch.cuh), in
+// the same units; false when the call does not qualify, with nothing enqueued.
+bool rts_pass_launch(const FiltParams<2, float> &, const LaunchReq &, const KfBufs<float> &, char *,
+                     const WsLayout &, cudaError_t *);
+bool rts_pass_launch(const FiltParams<4, float> &, const LaunchReq &, const KfBufs<float> &, char *,
+                     const WsLayout &, cudaError_t *);
+bool rts_pass_launch(const FiltParams<2, double> &, const LaunchReq &, const KfBufs<double> &, char *,
+                     const WsLayout &, cudaError_t *);
+bool rts_pass_launch(const FiltParams<4, double> &, const LaunchReq &, const KfBufs<double> &, char *,
+                     const WsLayout &, cudaError_t *);
 
 // The forward pass with the general or the low-rank operator forms, through
 // the requested scan algorithm (DLB_ONLY: always the decoupled look-back scan).
@@ -826,6 +836,12 @@ static cudaError_t launch_typed(const LaunchReq &q) {
     cudaError_t e = filter_pass<N, R, MODE, Src, THREADS, V, false>(fa, lowrank, ws, L, qz, q.loglik);
     if (e != cudaSuccess || q.op == KF_OP_FILTER_I) return e;
     if (q.op == KF_OP_RTS_I) {
+        if constexpr (N <= 4) {   // one sequence: the dedicated RTS kernel
+            if (q.scan == KF_SCAN_DLB_I && q.rts_kernel == 0 && !q.no_alloc) {
+                cudaError_t er = cudaSuccess;
+                if (rts_pass_launch(fa.src.prm, qz, buf, ws, L, &er)) return er;
+            }
+        }
         typename RtsRev<N, R, Src>::Args ra;
         ra.src = fa.src;
         ra.buf = buf;

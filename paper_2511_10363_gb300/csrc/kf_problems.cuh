@@ -482,6 +482,13 @@ struct FilterFwd {
 #pragma unroll
         for (int i = 0; i < S; ++i) c.v[Carry::oC + i] = e.v[Elem::oC + i];
     }
+    // A exactly zero: the element's (b, C) is what it makes of any carry
+    static KF_D bool zero_transition(const Elem &e) {
+        bool z = true;
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) z = z && e.v[Elem::oA + i] == R(0);
+        return z;
+    }
     // outputs of the position p (global index p) whose prefix carry is c
     static KF_D void emit(const Args &, int64_t, SegCursor &, const Carry &c, const R *, R *o1, R *o2, R *o3) {
         const R *b = c.v + Carry::ob, *C = c.v + Carry::oC;
@@ -692,6 +699,13 @@ struct TfRev {
 #pragma unroll
         for (int i = 0; i < S; ++i) c.v[Carry::oJ + i] = e.v[Elem::oJ + i];
     }
+    // A exactly zero: the element's (eta, J) is what it makes of any carry
+    static KF_D bool zero_transition(const Elem &e) {
+        bool z = true;
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) z = z && e.v[Elem::oA + i] == R(0);
+        return z;
+    }
     // merge with the filter record (Eqs. mean_tf_combination / cov_tf_combination)
     static KF_D void emit(const Args &, int64_t, SegCursor &, const Carry &c, const R *in, R *o1, R *o2, R *) {
         R rec[IN_REC], ms[N], Ps[S], full[N * N];
@@ -773,6 +787,13 @@ struct RtsRev {
         for (int i = 0; i < N; ++i) c.v[Carry::og + i] = e.v[Elem::og + i];
 #pragma unroll
         for (int i = 0; i < S; ++i) c.v[Carry::oL + i] = e.v[Elem::oL + i];
+    }
+    // E exactly zero: the element's (g, L) is what it makes of any carry
+    static KF_D bool zero_transition(const Elem &e) {
+        bool z = true;
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) z = z && e.v[Elem::oE + i] == R(0);
+        return z;
     }
     static KF_D void emit(const Args &, int64_t, SegCursor &, const Carry &c, const R *, R *o1, R *o2, R *) {
         R full[N * N];

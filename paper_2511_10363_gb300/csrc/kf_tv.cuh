@@ -390,6 +390,13 @@ struct FilterTv {
     static KF_D void combine(const Elem &x, const Elem &y, Elem &o) { op_lemma1<N, R, MODE>(x, y, o); }
     static KF_D void fold(const Args &, const SegCursor &, const Elem &x, const Elem &y, Elem &o) { combine(x, y, o); }
     static KF_D void apply(Carry &c, const Elem &e) { op_apply_fwd<N, R, MODE, false>(c, e, nullptr, nullptr); }
+    // the transition block exactly zero: the element's half is what it makes of any carry
+    static KF_D bool zero_transition(const Elem &e) {
+        bool z = true;
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) z = z && e.v[Elem::oA + i] == R(0);
+        return z;
+    }
     static KF_D void carry_of(const Elem &e, Carry &c) {
 #pragma unroll
         for (int i = 0; i < N; ++i) c.v[Carry::ob + i] = e.v[Elem::ob + i];
@@ -476,6 +483,13 @@ struct TfTv {
     static KF_D void combine(const Elem &x, const Elem &y, Elem &o) { op_lemma1<N, R, MODE>(y, x, o); }
     static KF_D void fold(const Args &, const SegCursor &, const Elem &x, const Elem &y, Elem &o) { combine(x, y, o); }
     static KF_D void apply(Carry &c, const Elem &e) { op_apply_rev<N, R, MODE>(c, e); }
+    // the transition block exactly zero: the element's half is what it makes of any carry
+    static KF_D bool zero_transition(const Elem &e) {
+        bool z = true;
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) z = z && e.v[Elem::oA + i] == R(0);
+        return z;
+    }
     static KF_D void carry_of(const Elem &e, Carry &c) {
 #pragma unroll
         for (int i = 0; i < N; ++i) c.v[Carry::oe + i] = e.v[Elem::oe + i];
@@ -542,6 +556,13 @@ struct RtsTv {
     static KF_D void combine(const Elem &x, const Elem &y, Elem &o) { op_lemma2<N, R>(y, x, o); }
     static KF_D void fold(const Args &, const SegCursor &, const Elem &x, const Elem &y, Elem &o) { combine(x, y, o); }
     static KF_D void apply(Carry &c, const Elem &e) { op_apply_rts<N, R>(c, e); }
+    // the transition block exactly zero: the element's half is what it makes of any carry
+    static KF_D bool zero_transition(const Elem &e) {
+        bool z = true;
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) z = z && e.v[Elem::oE + i] == R(0);
+        return z;
+    }
     static KF_D void carry_of(const Elem &e, Carry &c) {
 #pragma unroll
         for (int i = 0; i < N; ++i) c.v[Carry::og + i] = e.v[Elem::og + i];

@@ -149,8 +149,12 @@ KF_D int seg_slot(int c) { return P::REV ? C - 1 - c : c; }
 #ifndef KF_DLB_MINB_TF
 #define KF_DLB_MINB_TF 1
 #endif
+#ifndef KF_DLB_MINB_RTS256
+#define KF_DLB_MINB_RTS256 1
+#endif
 template <class P, int THREADS>
 constexpr int dlb_min_blocks() {
+    if (THREADS == 256) return P::KIND == 1 ? KF_DLB_MINB_RTS256 : 1;
     if (THREADS != 128) return 1;
     return P::KIND == 0 ? KF_DLB_MINB_FILTER : P::KIND == 1 ? KF_DLB_MINB_RTS : KF_DLB_MINB_TF;
 }
@@ -405,11 +409,25 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
     for (int i = 0; i < ES; ++i) tagg.v[i] = s_red[0][i];
 
     // publish the tile aggregate (tile 0 publishes its inclusive prefix
-    // directly); the release store orders the data stores before the flag
+    // directly); the release store orders the data stores before the flag.
+    // An aggregate whose transition block (A, or E for Lemma 2) is exactly
+    // zero -- a product of many steps that underflowed, or a segment start --
+    // makes its inclusive carry independent of the tiles before it: it is
+    // published at once (flag 2), so later look-backs stop there.
     constexpr int ESP = padded_size<Elem, R>();
+    const bool zt = tile > 0 && P::zero_transition(tagg);
     if (tile > 0 && tid == 0) {
-        store_vec(static_cast<R *>(ctl.agg) + int64_t(tile) * ESP, tagg);
-        st_release(ctl.flags + tile, 1);
+        if (zt) {
+            Carry inc;
+            P::carry_of(tagg, inc);
+            R *dst = static_cast<R *>(ctl.incl) + int64_t(tile) * CS;
+#pragma unroll
+            for (int i = 0; i < CS; ++i) dst[i] = inc.v[i];
+            st_release(ctl.flags + tile, 2);
+        } else {
+            store_vec(static_cast<R *>(ctl.agg) + int64_t(tile) * ESP, tagg);
+            st_release(ctl.flags + tile, 1);
+        }
     }
     __syncthreads();
     if (trace) trace[2] = global_ns();
@@ -539,11 +557,13 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
         if (lane == 0) {
 #pragma unroll
             for (int i = 0; i < CS; ++i) s_carry[i] = tc.v[i];
-            R *dst = static_cast<R *>(ctl.incl) + int64_t(tile) * CS;
+            if (!zt) {   // (already published when the transition is zero)
+                R *dst = static_cast<R *>(ctl.incl) + int64_t(tile) * CS;
 #pragma unroll
-            for (int i = 0; i < CS; ++i) dst[i] = inc.v[i];
-            __threadfence();
-            st_release(ctl.flags + tile, 2);
+                for (int i = 0; i < CS; ++i) dst[i] = inc.v[i];
+                __threadfence();
+                st_release(ctl.flags + tile, 2);
+            }
             if (trace) trace[12] = global_ns();
         }
     }

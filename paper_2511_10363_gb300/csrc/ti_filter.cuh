@@ -37,6 +37,7 @@
 #pragma once
 
 #include "kf_problems.cuh"
+#include "stage.cuh"
 
 namespace kfs {
 
@@ -287,14 +288,24 @@ KF_D void ti_emit(const TiArgs<N, R> &a, int64_t g, const R *b, const R *C, R *s
     }
 }
 
-// Shared-memory bytes of the record staging of one CTA: per warp, the next
-// CH records of its 32 runs, each run's chunk at an odd number of 16-byte
-// units so that the lanes' record stores hit distinct banks.
+// Per-warp shared memory of the staging: a ring of NST input buffers of the
+// warp's 32 runs of y (cp.async, chunks of CF steps in the fold, CH steps in
+// the carry pass: the two rings share the region), and in the carry pass the
+// next CH filter records of the 32 runs, each run's chunk at an odd number of
+// 16-byte units so that the lanes' record stores hit distinct banks.
+KF_HD constexpr int ti_al16(int x) { return (x + 15) / 16 * 16; }
 template <int N, typename R, int THREADS, int CH>
-KF_HD constexpr int ti_stage_bytes() {
-    constexpr int FB = FRec<N, R>::SIZE * int(sizeof(R));
-    return (THREADS / 32) * 32 * (((CH * FB / 16) | 1) * 16);
-}
+struct TiStage {
+    static constexpr int M = N / 2, NST = 4, CF = 4;
+    static constexpr int FB = FRec<N, R>::SIZE * int(sizeof(R));
+    static constexpr int YF = ti_al16(WarpStage<CF, M, R>::BYTES);    // one fold input buffer
+    static constexpr int YC = ti_al16(WarpStage<CH, M, R>::BYTES);    // one carry-pass input buffer
+    static constexpr int OUT = 32 * (((CH * FB / 16) | 1) * 16);  // the record buffer
+    static constexpr int warp_bytes(bool staged) {
+        return NST * YF > NST * YC + (staged ? OUT : 0) ? NST * YF : NST * YC + (staged ? OUT : 0);
+    }
+    static constexpr int bytes(bool staged) { return (THREADS / 32) * warp_bytes(staged); }
+};
 
 // Threads per CTA THREADS, records per staged chunk CH, MINB resident CTAs
 // per SM.
@@ -316,9 +327,12 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
     R *const rows = reinterpret_cast<R *>(dsm);
     R *const sets = rows + TT::al((a.K > 1 ? a.K - 1 : 0) * E);
     unsigned char *const stage = reinterpret_cast<unsigned char *>(sets + TT::al(TT::NSETS * TT::WES));
+    using ST = TiStage<N, R, THREADS, CH>;
+    constexpr int NST = ST::NST, CF = ST::CF;
     constexpr int RU = FR * int(sizeof(R)) / 16;              // 16-byte units of a record,
     constexpr int SEGU = CH * RU, STRU = SEGU | 1;            // of a run's chunk, and its odd stride
-    float4 *const wstage = a.frec ? reinterpret_cast<float4 *>(stage) + warp * 32 * STRU : nullptr;
+    unsigned char *const wbase = stage + warp * ST::warp_bytes(a.frec != nullptr);
+    float4 *const wstage = a.frec ? reinterpret_cast<float4 *>(wbase + NST * ST::YC) : nullptr;
 
     if (tid == 0) {
         s_tile = atomicAdd(a.counters, 1);
@@ -343,51 +357,71 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
     const int64_t r0 = (int64_t(tile) * THREADS + tid) * a.K;       // this thread's first position
     const int64_t r1 = r0 + a.K < treg ? r0 + a.K : treg;          // one past its last
 
-    // ---- 2. thread fold
+    // ---- 2. thread fold (y of the warp's 32 runs staged through a cp.async ring)
+    const int64_t wr0 = (int64_t(tile) * THREADS + warp * 32) * a.K;   // lane 0's first position
     R b[N], e[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) b[i] = e[i] = 0;
     {
-        int c = 0;
-#pragma unroll 4
-        for (int64_t p = r0; p < r1; ++p, ++c) {
-            R y[M];
-            ti_load_y<M, R>(a.y, p + 1, y);
-            if (c == 0) {
-                fresh_b_eta<N, M, R>(P, y, b, e);
-                continue;
-            }
-            const R *row = rows + (c - 1) * E;
-            const R *T1 = row, *T4 = row + NN, *T3U = row + NN + N * M;
-            R v[M];
+        auto fbuf = [&](int ch) { return wbase + (ch % NST) * ST::YF; };
+        const int nch = (a.K + CF - 1) / CF;   // the same for every lane
 #pragma unroll
-            for (int i = 0; i < M; ++i) {
-                R s = 0;
-#pragma unroll
-                for (int k = 0; k <= i; ++k) s += P.Linv[i * MAXNY + k] * y[k];
-#pragma unroll
-                for (int k = 0; k < N; ++k) s -= P.U[i * N + k] * b[k];
-                v[i] = s;
-            }
-            R nb[N];
-#pragma unroll
-            for (int r = 0; r < N; ++r) {
-                R s = 0;
-#pragma unroll
-                for (int j = 0; j < M; ++j) s += T4[r * M + j] * y[j];
-#pragma unroll
-                for (int k = 0; k < N; ++k) s += T1[r * N + k] * b[k];
-                nb[r] = s;
-            }
-#pragma unroll
-            for (int r = 0; r < N; ++r) {
-                R s = e[r];
-#pragma unroll
-                for (int i = 0; i < M; ++i) s += T3U[r * M + i] * v[i];
-                e[r] = s;
-                b[r] = nb[r];
-            }
+        for (int k = 0; k < NST - 1; ++k) {
+            if (k < nch) stage_load<CF, M, R>(a.y, wr0 + 1 + int64_t(k) * CF, a.K, a.T, fbuf(k), lane);
+            cp_async_commit();
         }
+#pragma unroll 1
+        for (int ch = 0; ch < nch; ++ch) {
+            const int ahead = ch + NST - 1;   // its buffer was last read in chunk ch - 1
+            if (ahead < nch) stage_load<CF, M, R>(a.y, wr0 + 1 + int64_t(ahead) * CF, a.K, a.T, fbuf(ahead), lane);
+            cp_async_commit();
+            cp_async_wait<NST - 1>();
+            __syncwarp();
+#pragma unroll
+            for (int cc = 0; cc < CF; ++cc) {
+                const int c = ch * CF + cc;
+                if (r0 + c >= r1) break;
+                R y[M];
+                load_rec<M>(y, stage_rec<CF, M, R>(fbuf(ch), lane, cc));
+                if (c == 0) {
+                    fresh_b_eta<N, M, R>(P, y, b, e);
+                    continue;
+                }
+                const R *row = rows + (c - 1) * E;
+                const R *T1 = row, *T4 = row + NN, *T3U = row + NN + N * M;
+                R v[M];
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    R s = 0;
+#pragma unroll
+                    for (int k = 0; k <= i; ++k) s += P.Linv[i * MAXNY + k] * y[k];
+#pragma unroll
+                    for (int k = 0; k < N; ++k) s -= P.U[i * N + k] * b[k];
+                    v[i] = s;
+                }
+                R nb[N];
+#pragma unroll
+                for (int r = 0; r < N; ++r) {
+                    R s = 0;
+#pragma unroll
+                    for (int j = 0; j < M; ++j) s += T4[r * M + j] * y[j];
+#pragma unroll
+                    for (int k = 0; k < N; ++k) s += T1[r * N + k] * b[k];
+                    nb[r] = s;
+                }
+#pragma unroll
+                for (int r = 0; r < N; ++r) {
+                    R s = e[r];
+#pragma unroll
+                    for (int i = 0; i < M; ++i) s += T3U[r * M + i] * v[i];
+                    e[r] = s;
+                    b[r] = nb[r];
+                }
+            }
+            __syncwarp();
+        }
+        cp_async_wait<0>();
+        __syncwarp();
     }
     if (trace) trace[1] = ti_ns();
 
@@ -497,9 +531,17 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
         // back off exponentially between rounds, so that the waiting tiles
         // keep the L2 free for the tiles still working; the rest of the CTA
         // waits at the barrier
+        // X_{i-1} exactly zero (the map of a long tile underflows): b_{i-1} =
+        // u_{i-1} + X_{i-1} (...) is u_{i-1} exactly, so only tile i-1 is needed
+        bool xz = true;
+        {
+            const R *Xp = a.tab + a.off_tiles + int64_t(tile - 1) * TT::TES + 2 * S;
+#pragma unroll
+            for (int i = 0; i < NN; ++i) xz = xz && __ldg(Xp + i) == R(0);
+        }
         if (warp == NW - 1) {
             bool ok = true;
-            for (int q0 = 0; q0 < tile && ok; q0 += 32) {
+            for (int q0 = xz ? tile - 1 : 0; q0 < tile && ok; q0 += 32) {
                 const int q = q0 + lane;
                 bool seen = q >= tile || ti_ld_relaxed(a.flags + q) != 0;
                 unsigned ns = 32;
@@ -522,7 +564,14 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
         if (s_abort) return;
         const int lbt = 32 * a.lbw;
         const int vv = (tile + lbt - 1) / lbt;
-        if (tid < lbt) {
+        if (xz) {
+            if (tid == 0) {
+                asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                const R *up = a.ubuf + int64_t(tile - 1) * TT::UP;
+#pragma unroll
+                for (int i = 0; i < N; ++i) s_tb[i] = __ldcg(up + i);
+            }
+        } else if (tid < lbt) {
             R F[NN], v[N];
             bool have = false;
 #pragma unroll
@@ -617,7 +666,7 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
         __syncthreads();
         if (trace) trace[6] = s_twait;
         if (trace) trace[14] = ti_ns();
-        if (tid == 0) {   // warps in order: only the mean of the composition is needed
+        if (tid == 0 && !xz) {   // warps in order: only the mean of the composition is needed
             R v[N];
 #pragma unroll
             for (int i = 0; i < N; ++i) v[i] = s_lx[0][NN + i];
@@ -730,10 +779,21 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
     }
     {
         // chunks of CH steps, the same count for every lane of the warp (the
-        // lanes share each chunk's store)
+        // lanes share each chunk's y ring buffer and record store)
         const int nch = (a.K + CH - 1) / CH;
+        auto cbuf = [&](int ch) { return wbase + (ch % NST) * ST::YC; };
+#pragma unroll
+        for (int k = 0; k < NST - 1; ++k) {
+            if (k < nch) stage_load<CH, M, R>(a.y, wr0 + 1 + int64_t(k) * CH, a.K, a.T, cbuf(k), lane);
+            cp_async_commit();
+        }
 #pragma unroll 1
         for (int ch = 0; ch < nch; ++ch) {
+            const int ahead = ch + NST - 1;
+            if (ahead < nch) stage_load<CH, M, R>(a.y, wr0 + 1 + int64_t(ahead) * CH, a.K, a.T, cbuf(ahead), lane);
+            cp_async_commit();
+            cp_async_wait<NST - 1>();
+            __syncwarp();
             R *buf = wstage ? reinterpret_cast<R *>(wstage + lane * STRU) : nullptr;
             const int64_t p0 = r0 + int64_t(ch) * CH;
             const int cnt = int(r1 - p0 < CH ? (r1 - p0 > 0 ? r1 - p0 : 0) : CH);
@@ -743,7 +803,7 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
                 if (cc >= cnt) break;
                 const int64_t g = p0 + cc + 1;   // record of time k = g + 1
                 R y[M], bk[N], ek[N];
-                ti_load_y<M, R>(a.y, g, y);
+                load_rec<M>(y, stage_rec<CH, M, R>(cbuf(ch), lane, cc));
                 fresh_b_eta<N, M, R>(P, y, bk, ek);
                 if (a.want_ll) {
                     R yt[M];
@@ -763,21 +823,35 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
                 ti_emit<N, R>(a, g, c.v + FwdCarry<N, R>::ob, c.v + FwdCarry<N, R>::oC, buf ? buf + cc * FR : nullptr);
             }
             ll += double(llc);
+            __syncwarp();   // every lane is done with this chunk's y buffer and records
             if (wstage) {   // the warp's 32 chunks, each run's records contiguous in memory
-                __syncwarp();
+                // a lane moves the same unit o of every run it visits (SEGU, a
+                // power of two, divides 32 when it is at most 32)
                 float4 *g = reinterpret_cast<float4 *>(a.frec);
-                const int64_t wr0 = (int64_t(tile) * THREADS + warp * 32) * a.K;   // lane 0's first position
+                if constexpr (SEGU <= 32 && (32 % SEGU) == 0) {
+                    constexpr int STEP = 32 / SEGU;
+                    const int o = lane % SEGU, rc = o / RU, ru = o % RU;
+#pragma unroll
+                    for (int run = lane / SEGU; run < 32; run += STEP) {
+                        const int64_t rs = wr0 + int64_t(run) * a.K;               // the run's first position
+                        const int64_t re = rs + a.K < treg ? rs + a.K : treg;      // one past its last
+                        const int64_t pos = rs + int64_t(ch) * CH + rc;
+                        if (pos < re) g[(pos + 1) * RU + ru] = wstage[run * STRU + o];
+                    }
+                } else {
 #pragma unroll 2
-                for (int idx = lane; idx < 32 * SEGU; idx += 32) {
-                    const int run = idx / SEGU, o = idx - run * SEGU;
-                    const int64_t rs = wr0 + int64_t(run) * a.K;               // the run's first position
-                    const int64_t re = rs + a.K < treg ? rs + a.K : treg;      // one past its last
-                    const int64_t pos = rs + int64_t(ch) * CH + o / RU;
-                    if (pos < re) g[(pos + 1) * RU + o % RU] = wstage[run * STRU + o];
+                    for (int idx = lane; idx < 32 * SEGU; idx += 32) {
+                        const int run = idx / SEGU, o = idx - run * SEGU;
+                        const int64_t rs = wr0 + int64_t(run) * a.K;
+                        const int64_t re = rs + a.K < treg ? rs + a.K : treg;
+                        const int64_t pos = rs + int64_t(ch) * CH + o / RU;
+                        if (pos < re) g[(pos + 1) * RU + o % RU] = wstage[run * STRU + o];
+                    }
                 }
                 __syncwarp();
             }
         }
+        cp_async_wait<0>();
     }
     if (trace) trace[5] = ti_ns();
 

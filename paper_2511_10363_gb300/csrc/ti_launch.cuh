@@ -144,33 +144,44 @@ struct TiCfg {
     static constexpr int CH = (sizeof(R) == 8 && THREADS == 256) ? 1 : 2;
     static constexpr int MINB = THREADS == 256 ? 2 : 4;
     static constexpr int KT = FoldTab<N, N / 2, R>::KT;   // fold rows at most
-    static int smem(bool staged) {
+    // dynamic shared memory of a launch with K positions per thread: fold
+    // rows (K - 1 of them), coefficient sets, staging
+    static int smem(bool staged, int K) {
         using TT = TiTab<N, R>;
-        return int(sizeof(R)) * (TT::al(KT * TT::E) + TT::al(TT::NSETS * TT::WES)) +
-               (staged ? ti_stage_bytes<N, R, THREADS, CH>() : 0);
+        return int(sizeof(R)) * (TT::al((K > 1 ? K - 1 : 0) * TT::E) + TT::al(TT::NSETS * TT::WES)) +
+               TiStage<N, R, THREADS, CH>::bytes(staged);
     }
 };
 
+// Resident CTAs on the device for a launch with `smem` bytes of dynamic
+// shared memory (occupancy query, cached per device and size).
 template <int N, typename R, int THREADS>
-static int ti_resident(int dev, bool staged) {
+static int ti_resident(int dev, int smem) {
     using CF = TiCfg<N, R, THREADS>;
     static std::mutex mu;
-    static int val[64][2];
+    static bool attr[64];
+    static int key_dev[32], key_smem[32], val[32], n = 0;
     std::lock_guard<std::mutex> lk(mu);
     if (dev < 0 || dev >= 64) return 0;
-    int &v = val[dev][staged ? 1 : 0];
-    if (v == 0) {
-        auto kern = ti_filter_kernel<N, R, THREADS, CF::CH, CF::MINB>;
-        const int smem = CF::smem(staged);
-        // the attribute allows the larger (staged) size, whichever launch comes first
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::smem(true)) != cudaSuccess)
+    for (int i = 0; i < n; ++i)
+        if (key_dev[i] == dev && key_smem[i] == smem) return val[i];
+    auto kern = ti_filter_kernel<N, R, THREADS, CF::CH, CF::MINB>;
+    if (!attr[dev]) {   // allow the largest launch once per device
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::smem(true, CF::KT + 1)) !=
+            cudaSuccess)
             return 0;
-        int sms = 0, per = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, THREADS, smem) != cudaSuccess || per < 1) return 0;
-        v = sms * per;
+        attr[dev] = true;
     }
-    return v;
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, THREADS, smem) != cudaSuccess || per < 1) return 0;
+    if (n < 32) {
+        key_dev[n] = dev;
+        key_smem[n] = smem;
+        val[n] = sms * per;
+        ++n;
+    }
+    return sms * per;
 }
 
 // Launches the forward filter scan on the table kernel.  Returns false, with
@@ -185,18 +196,27 @@ static bool ti_filter_run(const FiltParams<N, R> &prm, const LaunchReq &q, const
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     const bool staged = buf.frec != nullptr;
-    const int resident = ti_resident<N, R, THREADS>(dev, staged);
-    if (resident < 1) return false;
     const int64_t treg = q.T - 1;
+    // one wave of resident CTAs; the fold rows in shared memory depend on K,
+    // so the plan is refined once with the shared memory of the chosen K
+    auto plan_k = [&](int resident) -> int64_t {
+        int64_t K = (treg + int64_t(resident) * THREADS - 1) / (int64_t(resident) * THREADS);
+        if (K < 1) K = 1;
+        return K > CF::KT + 1 ? CF::KT + 1 : K;
+    };
     int64_t K;
     if (q.k_override > 0) {
         K = q.k_override;
+        if (K > CF::KT + 1) return false;
+        if (ti_resident<N, R, THREADS>(dev, CF::smem(staged, int(K))) < 1) return false;
     } else {
-        K = (treg + int64_t(resident) * THREADS - 1) / (int64_t(resident) * THREADS);
-        if (K < 1) K = 1;
-        if (K > CF::KT + 1) K = CF::KT + 1;
+        int resident = ti_resident<N, R, THREADS>(dev, CF::smem(staged, 1));
+        if (resident < 1) return false;
+        K = plan_k(resident);
+        const int r2 = ti_resident<N, R, THREADS>(dev, CF::smem(staged, int(K)));
+        if (r2 < 1) return false;
+        if (r2 < resident) K = plan_k(r2);
     }
-    if (K > CF::KT + 1) return false;
     int64_t nt = (treg + THREADS * K - 1) / (THREADS * K);
     if (nt < 1) nt = 1;
     if (nt > KF_MAX_TILES) return false;
@@ -257,7 +277,7 @@ static bool ti_filter_run(const FiltParams<N, R> &prm, const LaunchReq &q, const
         *err = e;
         return true;
     }
-    const int smem = CF::smem(staged);
+    const int smem = CF::smem(staged, int(K));
     if (debug_on())
         fprintf(stderr, "[kfscan] ti filter: T=%lld tiles=%d K=%lld threads=%d smem=%d\n", (long long)q.T, ntiles,
                 (long long)K, THREADS, smem);
