@@ -36,71 +36,62 @@ SM_MAX_MHZ = 2070.0
 
 
 # ------------------------------------------------------------------ work model
-# FMA counts of the operator code in kf_math.cuh, counted loop by loop, with
-# n = nx, m = ny, S = n(n+1)/2; an FMA counts 2 flops, a reciprocal 1.
+# Flops per time step of the one-sequence kernels (time-invariant model,
+# m = n/2), counted loop by loop from their step code in kf_steps.cuh with
+# n = nx, m = ny, S = n(n+1)/2: an add, subtract or multiply counts 1 (a
+# multiply-add 2), a reciprocal, square root or log 1.  tests/test_flop_count.py
+# checks each against the library's own count of that code
+# (kf_count_step_flops).
 
-def lemma1_flops(n):
-    S = n * (n + 1) // 2
-    fma = 5 * n ** 3 + 3 * S * n + 5 * n * n + (n - 1) * (3 * n * n - n) // 2
-    return 2 * fma + (3 * n * n - n) // 2 + n
+def table_fold_flops(n, m):
+    """One step of the filter's table-driven thread fold:
+    v = L^{-1} y - U b, b <- T1 b + T4 y, eta <- eta + T3U v."""
+    return m * (m + 1) + 6 * n * m + 2 * n * n
 
 
-def lemma2_flops(n):
-    S = n * (n + 1) // 2
-    return 2 * (2 * n ** 3 + n * n + S * n)
+def filter_carry_flops(n, m, loglik=False):
+    """One step of the filter's carry pass: b_k = K y, eta_k = G y, and the
+    rank-m form of Lemma 1 on the carry (b, C); with the innovation term."""
+    S, Sm = n * (n + 1) // 2, m * (m + 1) // 2
+    inv = {1: 2, 2: 8}[m]          # m x m inverse and its log-determinant
+    f = (4 * n * m                  # b_k, eta_k
+         + 2 * m * n * n + 2 * n * Sm + inv + 2 * m * m * n + 2 * m * S   # G = U C, I + G U^T, W, WG, D
+         + 2 * m * n + 2 * m * m + n * (2 * m + 2 * n)                    # U b, W U b, u
+         + 2 * n ** 3 + 2 * n * n + 2 * n * S)                           # A D, b, C
+    if loglik:
+        f += m * (m + 1) + m + 3 * m * m + 3
+    return f
 
 
 def rts_build_flops(n):
+    """E = P F^T P_{k+1|k}^{-1} (Cholesky of P_{k+1|k}), F xbar, P_{k+1|k}."""
     S = n * (n + 1) // 2
-    fma = n ** 3 + (S * n + sum(j for i in range(n) for j in range(i + 1))) + n * n * (n - 1) + 2 * n * n + S * n
-    return 2 * fma + (S - n) + 2 * n * n + 2 * n
+    return 2 * n ** 3 + 2 * n * S + (n - 1) * n * (n + 1) // 3 + 2 * n + (S - n) + 2 * n ** 3 + 2 * n * n
 
 
-def lemma1_lr_flops(n, m):
-    """Lemma 1 with a fresh right operand whose J has rank m (Woodbury form)."""
-    S, Sm = n * (n + 1) // 2, m * (m + 1) // 2
-    fma = (m * n * n + Sm * n + m * n * m + S * m + m * n * n + m * n * m + n * n * m + m * n + m * m + n * (m + n)
-           + n * m + 2 * n ** 3 + n * n + S * n + n * n + n * n * m + S * n)
-    inv = {1: 2, 2: 8}.get(m, 4 * m ** 3)
-    return 2 * fma + inv
+def rts_direct_flops(n):
+    """(g, L) <- (xbar + E (g - F xbar), P + E (L - P_{k+1|k}) E^T)."""
+    S = n * (n + 1) // 2
+    return n + S + 2 * n * n + 2 * n ** 3 + 2 * n * S
 
 
-def apply_lr_flops(n, m, loglik=True):
-    """(b, C) half of Lemma 1 for a fresh element (Woodbury form)."""
-    S, Sm = n * (n + 1) // 2, m * (m + 1) // 2
-    fma = m * n * n + Sm * n + m * n * m + S * m + m * n + m * m + n * (m + n) + n ** 3 + n + S * n
-    inv = {1: 2, 2: 8}.get(m, 4 * m ** 3)
-    f = 2 * fma + inv
-    if loglik:
-        f += 2 * (m * (m + 1) // 2 + m + m * m) + 10
-    return f
+def rts_fold_flops(n):
+    return rts_build_flops(n) + 2 * n ** 3 + rts_direct_flops(n)
 
 
-def table_fold_flops(n, m):
-    """One step of the table-driven thread fold (time-invariant model, m = n/2):
-    v = L^{-1} y - U b, b <- T1 b + T4 y, eta <- eta + T3U v."""
-    fma = m * (m + 1) // 2 + m * n + n * m + n * n + n * m
-    return 2 * fma
+def rts_carry_flops(n):
+    return rts_build_flops(n) + rts_direct_flops(n)
 
 
 def filter_step_flops(n, m, loglik=True):
-    """Per time step of the filter scan as run: one fold step (the fold table
-    when m = n/2, else one Lemma 1 combine) and one carry application (rank-m
-    form when m = n/2), plus building (b_k, eta_k)."""
-    if 2 * m == n:
-        return table_fold_flops(n, m) + apply_lr_flops(n, m, loglik) + 4 * n * m
-    f = lemma1_flops(n) + lemma1_flops(n) // 2 + 4 * n * m
-    if loglik:
-        f += 2 * (m * n + m * m + m + 2 * n * n + n) + n
-    return f
+    """Per time step of the filter pass as run: one fold step and one carry step."""
+    return table_fold_flops(n, m) + filter_carry_flops(n, m, loglik)
 
 
 def rts_step_flops(n):
-    """Per time step of the RTS scan as run: build (E, g, L), one Lemma 2
-    fold and one carry application."""
-    S = n * (n + 1) // 2
-    apply = 2 * (n ** 3 + S * n + n * n)
-    return lemma2_flops(n) + apply + rts_build_flops(n)
+    """Per time step of the RTS pass as run: the element built in the fold and
+    again in the carry pass."""
+    return rts_fold_flops(n) + rts_carry_flops(n)
 
 
 def step_bytes(n, m, w):
@@ -955,7 +946,7 @@ def main():
 
     # ---- roofline of the dominant kernel
     fb, rb = step_bytes(nx, ny, w)
-    f_flops = filter_step_flops(nx, ny)
+    f_flops = filter_step_flops(nx, ny, want_ll)
     r_flops = rts_step_flops(nx)
     fma_peak = kf.measure_fma_peak(fp64=(args.precision == "fp64"))
     if args.precision == "fp64":

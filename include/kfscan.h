@@ -383,6 +383,17 @@ typedef enum {
 kf_status_t kf_set_option(kf_option_t opt, int64_t value);
 int64_t kf_get_option(kf_option_t opt); /* -1 for an unknown option */
 
+/* Flops per time step of the one-sequence kernels, counted from their own
+ * step code (the step functions run on the host with a counting number
+ * type): step 0 = one step of the table-driven thread fold of the filter
+ * scan, 1 = one step of its carry pass, 2 = the same with the log-likelihood
+ * term, 3 = one step of the RTS pass's thread fold, 4 = one step of its carry
+ * pass.  nx = 2 or 4 (ny = nx / 2).  counts[6] receives the total (an
+ * add, subtract or multiply counts 1, so a multiply-add 2; a reciprocal,
+ * square root or log 1), then adds, multiplies, reciprocals, square roots,
+ * logs.  Host only.  KF_ERR_ARG for another nx or step. */
+kf_status_t kf_count_step_flops(int nx, int step, int64_t *counts);
+
 /* Kernel accounting (diagnostics for benchmarks).  The library counts every
  * kernel it launches, by kind.  While timing is enabled it also brackets each
  * scan (one kernel for the decoupled look-back scan; the whole level-by-level

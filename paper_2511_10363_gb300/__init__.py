@@ -123,6 +123,8 @@ def lib():
         L.kf_tv_two_filter_smooth.argtypes = [TP, i64, vp, i, i, vp, vp, vp, vp, vp, vp, vp]
         for f in ("kf_tv_filter", "kf_tv_rts_smooth", "kf_tv_two_filter_smooth"):
             getattr(L, f).restype = ctypes.c_int
+        L.kf_count_step_flops.argtypes = [i, i, ctypes.POINTER(ctypes.c_int64)]
+        L.kf_count_step_flops.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -618,3 +620,14 @@ def kf_tuning_load(path):
 
 def kf_tuning_clear():
     _check(lib().kf_tuning_clear(), "kf_tuning_clear")
+
+
+STEP_KINDS = {"filter_fold": 0, "filter_carry": 1, "filter_carry_loglik": 2, "rts_fold": 3, "rts_carry": 4}
+
+
+def kf_count_step_flops(nx, step):
+    """Flops of one time step of a kernel phase, counted from the kernels'
+    own step code (kfscan.h): dict with total, add, mul, rcp, sqrt, log."""
+    c = (ctypes.c_int64 * 6)()
+    _check(lib().kf_count_step_flops(int(nx), STEP_KINDS.get(step, step), c), "kf_count_step_flops")
+    return dict(zip(("total", "add", "mul", "rcp", "sqrt", "log"), [int(v) for v in c]))

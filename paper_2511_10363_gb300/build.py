@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "_build", "libkfscan.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = (["kf_api.cu", "kf_serve.cu", "kf_n4_f32_t256.cu", "kf_tv_n2.cu", "kf_tv_n4.cu", "kf_tv_n8.cu",
-          "ti_n4_f32.cu", "ti_n2_f32.cu", "ti_n4_f64.cu", "ti_n2_f64.cu"]
+          "ti_n4_f32.cu", "ti_n2_f32.cu", "ti_n4_f64.cu", "ti_n2_f64.cu", "flop_count.cpp"]
          + ["kf_n%d_%s.cu" % (n, p) for n in (8, 4, 2) for p in ("f64", "mix", "f32")]
          + ["kf_n%d_%s_batch.cu" % (n, p) for n, p in ((8, "f64"), (8, "mix"), (8, "f32"), (4, "f64"), (4, "mix"))])
 
@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(u):
         src = os.path.join(CSRC, u)
-        obj = os.path.join(BUILD, u.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(u)[0] + ".o")
         cmd = [cc, "-c", src, "-o", obj] + flags
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

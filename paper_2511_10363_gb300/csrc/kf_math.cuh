@@ -173,7 +173,9 @@ struct FiltParams {
 // hardware approximations (PTX rcp.approx / sqrt.approx, MUFU log2; relative
 // error about 2^-23, a few ulp for the log), far below the FP32 tolerance of
 // the outputs and cheaper than the correctly rounded sequences.  FP64:
-// correctly rounded.
+// correctly rounded.  (A host build of these headers, the flop counter of
+// flop_count.cpp, supplies its own overloads for its counting type.)
+#if defined(__CUDACC__)
 KF_D float recip(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -188,6 +190,7 @@ KF_D float ksqrt(float x) {
 KF_D double ksqrt(double x) { return sqrt(x); }
 KF_D float klog(float x) { return __logf(x); }
 KF_D double klog(double x) { return log(x); }
+#endif
 
 // X = (I + C J)^{-1} for packed symmetric C, J, by Gauss-Jordan elimination
 // with partial pivoting in precision T.  Returns sum log|pivot| = log det(I + C J)

@@ -23,6 +23,7 @@
 #pragma once
 
 #include "kf_problems.cuh"
+#include "kf_steps.cuh"
 #include "stage.cuh"
 
 namespace kfs {
@@ -44,113 +45,6 @@ struct RsArgs {
     uint64_t *trace;
     int trace_cap;
 };
-
-// Pieces of the element of time k: E = P F^T P_{k+1|k}^{-1}, F xbar and
-// P_{k+1|k} (packed), from the filter record (xbar, packed P).  last: E = 0.
-template <int N, typename R>
-KF_D void rs_build(const RsArgs<N, R> &a, bool last, const R *x, const R *P, R *E, R *Fx, R *Pp) {
-    if (last) {
-#pragma unroll
-        for (int i = 0; i < N * N; ++i) E[i] = 0;
-#pragma unroll
-        for (int i = 0; i < N; ++i) Fx[i] = 0;
-#pragma unroll
-        for (int i = 0; i < N * (N + 1) / 2; ++i) Pp[i] = 0;
-        return;
-    }
-    R U[N * N];   // F P
-#pragma unroll
-    for (int r = 0; r < N; ++r)
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-            R s = 0;
-#pragma unroll
-            for (int k = 0; k < N; ++k) s += a.F[r * N + k] * P[si(N, k, c)];
-            U[r * N + c] = s;
-        }
-    R Lc[N * (N + 1) / 2], dinv[N];   // P_{k+1|k} = U F^T + Q, its Cholesky factor
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j) {
-            R s = a.Q[su(N, j, i)];
-#pragma unroll
-            for (int k = 0; k < N; ++k) s += U[i * N + k] * a.F[j * N + k];
-            Pp[su(N, j, i)] = s;
-#pragma unroll
-            for (int k = 0; k < j; ++k) s -= Lc[i * (i + 1) / 2 + k] * Lc[j * (j + 1) / 2 + k];
-            if (i == j) {
-                const R d = ksqrt(s);
-                Lc[i * (i + 1) / 2 + i] = d;
-                dinv[i] = recip(d);
-            } else {
-                Lc[i * (i + 1) / 2 + j] = s * dinv[j];
-            }
-        }
-    // E^T = P_{k+1|k}^{-1} U, column by column (forward, then backward substitution)
-#pragma unroll
-    for (int c = 0; c < N; ++c) {
-        R z[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            R s = U[i * N + c];
-#pragma unroll
-            for (int k = 0; k < i; ++k) s -= Lc[i * (i + 1) / 2 + k] * z[k];
-            z[i] = s * dinv[i];
-        }
-#pragma unroll
-        for (int i = N - 1; i >= 0; --i) {
-            R s = z[i];
-#pragma unroll
-            for (int k = i + 1; k < N; ++k) s -= Lc[k * (k + 1) / 2 + i] * E[c * N + k];
-            E[c * N + i] = s * dinv[i];   // E[c][i] = (E^T)[i][c]
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < N; ++r) {
-        R s = 0;
-#pragma unroll
-        for (int k = 0; k < N; ++k) s += a.F[r * N + k] * x[k];
-        Fx[r] = s;
-    }
-}
-
-// (g, L) <- (xbar + E (g - F xbar), P + E (L - P_{k+1|k}) E^T)
-template <int N, typename R>
-KF_D void rs_direct(const R *E, const R *Fx, const R *Pp, const R *x, const R *P, R *g, R *L) {
-    constexpr int S = N * (N + 1) / 2;
-    R d[N], D[S];
-#pragma unroll
-    for (int i = 0; i < N; ++i) d[i] = g[i] - Fx[i];
-#pragma unroll
-    for (int i = 0; i < S; ++i) D[i] = L[i] - Pp[i];
-#pragma unroll
-    for (int r = 0; r < N; ++r) {
-        R s = x[r];
-#pragma unroll
-        for (int k = 0; k < N; ++k) s += E[r * N + k] * d[k];
-        g[r] = s;
-    }
-    R ED[N * N];
-#pragma unroll
-    for (int r = 0; r < N; ++r)
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-            R s = 0;
-#pragma unroll
-            for (int k = 0; k < N; ++k) s += E[r * N + k] * D[si(N, k, c)];
-            ED[r * N + c] = s;
-        }
-#pragma unroll
-    for (int r = 0; r < N; ++r)
-#pragma unroll
-        for (int c = r; c < N; ++c) {
-            R s = P[su(N, r, c)];
-#pragma unroll
-            for (int k = 0; k < N; ++k) s += ED[r * N + k] * E[c * N + k];
-            L[su(N, r, c)] = s;
-        }
-}
 
 KF_D int rs_ld_relaxed(const int *p) {
     int v;
@@ -262,21 +156,7 @@ __global__ void __launch_bounds__(THREADS, MINB) rts_kernel(const __grid_constan
 #pragma unroll 1
         for (int64_t p = r0; p < r1; ++p) {
             if (p + 1 < r1) load_rec<FR>(nxt, a.frec + (T - 2 - p) * FR);   // the next record, in flight
-            R E[NN], Fx[N], Pp[S];
-            rs_build<N, R>(a, p == 0, rec, rec + N, E, Fx, Pp);
-            R nE[NN];   // E_agg <- E_k E_agg
-#pragma unroll
-            for (int r = 0; r < N; ++r)
-#pragma unroll
-                for (int c = 0; c < N; ++c) {
-                    R s = 0;
-#pragma unroll
-                    for (int k = 0; k < N; ++k) s += E[r * N + k] * agg.v[El::oE + k * N + c];
-                    nE[r * N + c] = s;
-                }
-            rs_direct<N, R>(E, Fx, Pp, rec, rec + N, agg.v + El::og, agg.v + El::oL);
-#pragma unroll
-            for (int i = 0; i < NN; ++i) agg.v[El::oE + i] = nE[i];
+            rs_fold_step<N, R>(a.F, a.Q, p == 0, rec, agg.v + El::oE, agg.v + El::og, agg.v + El::oL);
 #pragma unroll
             for (int i = 0; i < FR; ++i) rec[i] = nxt[i];
         }
@@ -509,9 +389,7 @@ __global__ void __launch_bounds__(THREADS, MINB) rts_kernel(const __grid_constan
                 const int64_t p = r0 + int64_t(ch) * CH + cc;
                 if (p >= r1) break;
                 if (p + 1 < r1) load_rec<FR>(nxt, a.frec + (T - 2 - p) * FR);
-                R E[NN], Fx[N], Pp[S];
-                rs_build<N, R>(a, p == 0, rec, rec + N, E, Fx, Pp);
-                rs_direct<N, R>(E, Fx, Pp, rec, rec + N, c.v + Ca::og, c.v + Ca::oL);
+                rs_carry_step<N, R>(a.F, a.Q, p == 0, rec, c.v + Ca::og, c.v + Ca::oL);
                 const int slot = CH - 1 - cc;   // records ascend in time within a chunk
                 store_rec<N>(stage_rec<CH, N, R>(mbuf, lane, slot), c.v + Ca::og);
                 R full[NN];

@@ -37,6 +37,7 @@
 #pragma once
 
 #include "kf_problems.cuh"
+#include "kf_steps.cuh"
 #include "stage.cuh"
 
 namespace kfs {
@@ -387,36 +388,7 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
                     fresh_b_eta<N, M, R>(P, y, b, e);
                     continue;
                 }
-                const R *row = rows + (c - 1) * E;
-                const R *T1 = row, *T4 = row + NN, *T3U = row + NN + N * M;
-                R v[M];
-#pragma unroll
-                for (int i = 0; i < M; ++i) {
-                    R s = 0;
-#pragma unroll
-                    for (int k = 0; k <= i; ++k) s += P.Linv[i * MAXNY + k] * y[k];
-#pragma unroll
-                    for (int k = 0; k < N; ++k) s -= P.U[i * N + k] * b[k];
-                    v[i] = s;
-                }
-                R nb[N];
-#pragma unroll
-                for (int r = 0; r < N; ++r) {
-                    R s = 0;
-#pragma unroll
-                    for (int j = 0; j < M; ++j) s += T4[r * M + j] * y[j];
-#pragma unroll
-                    for (int k = 0; k < N; ++k) s += T1[r * N + k] * b[k];
-                    nb[r] = s;
-                }
-#pragma unroll
-                for (int r = 0; r < N; ++r) {
-                    R s = e[r];
-#pragma unroll
-                    for (int i = 0; i < M; ++i) s += T3U[r * M + i] * v[i];
-                    e[r] = s;
-                    b[r] = nb[r];
-                }
+                ti_fold_step<N, M, R>(P, rows + (c - 1) * E, y, b, e);
             }
             __syncwarp();
         }
@@ -802,24 +774,10 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
             for (int cc = 0; cc < CH; ++cc) {
                 if (cc >= cnt) break;
                 const int64_t g = p0 + cc + 1;   // record of time k = g + 1
-                R y[M], bk[N], ek[N];
+                R y[M];
                 load_rec<M>(y, stage_rec<CH, M, R>(cbuf(ch), lane, cc));
-                fresh_b_eta<N, M, R>(P, y, bk, ek);
-                if (a.want_ll) {
-                    R yt[M];
-#pragma unroll
-                    for (int i = 0; i < M; ++i) {
-                        R s = 0;
-#pragma unroll
-                        for (int k = 0; k <= i; ++k) s += P.Linv[i * MAXNY + k] * y[k];
-                        yt[i] = s;
-                    }
-                    R q, ld;
-                    apply_fwd_lr_parts<N, M, R, 0, true>(c, P.A, bk, P.C, ek, P.U, yt, &q, &ld);
-                    llc += R(-0.5) * (q + ld + P.llc_r);
-                } else {
-                    apply_fwd_lr_parts<N, M, R, 0, false>(c, P.A, bk, P.C, ek, P.U, nullptr, nullptr, nullptr);
-                }
+                if (a.want_ll) llc += ti_carry_step<N, M, R, true>(P, y, c);
+                else ti_carry_step<N, M, R, false>(P, y, c);
                 ti_emit<N, R>(a, g, c.v + FwdCarry<N, R>::ob, c.v + FwdCarry<N, R>::oC, buf ? buf + cc * FR : nullptr);
             }
             ll += double(llc);
