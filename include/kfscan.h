@@ -93,7 +93,8 @@ typedef enum {
     KF_ERR_TIMEOUT = 5,  /* a bounded inter-block wait in a kernel ran out   */
     KF_ERR_BUDGET = 6,   /* serving: job larger than the device budget       */
     KF_ERR_BUSY = 7,     /* serving: queue full / unknown job id             */
-    KF_ERR_CAPACITY = 8  /* request larger than a fixed scratch capacity     */
+    KF_ERR_CAPACITY = 8, /* request larger than a fixed scratch capacity     */
+    KF_ERR_CANCELLED = 9 /* server job cancelled before it started          */
 } kf_status_t;
 
 typedef struct {
@@ -264,6 +265,11 @@ kf_status_t kf_batch_graph_destroy(kf_batch_graph_t *graph);
  *     done, KF_ERR_BUSY for an unknown id.
  *   - kf_server_wait: blocks until the job is done (KF_ERR_TIMEOUT after
  *     timeout_s seconds).  kf_server_release forgets a done job.
+ *   - kf_server_cancel: takes a job that is still queued out of the queue;
+ *     it is then done with status KF_ERR_CANCELLED (poll and wait report
+ *     it) and its output buffers are not touched.  A job already in a batch
+ *     on the GPU, or done, returns KF_ERR_BUSY and runs to its end; an
+ *     unknown id returns KF_ERR_BUSY too.
  *   - kf_server_destroy: finishes the queued and running jobs, then frees
  *     the arena and streams. */
 typedef struct kf_server kf_server_t;
@@ -273,6 +279,7 @@ kf_status_t kf_server_submit(kf_server_t *srv, kf_op_t op, const kf_model_t *mod
 kf_status_t kf_server_poll(kf_server_t *srv, int64_t job_id, int *done, double *info);
 kf_status_t kf_server_wait(kf_server_t *srv, int64_t job_id, double timeout_s);
 kf_status_t kf_server_release(kf_server_t *srv, int64_t job_id);
+kf_status_t kf_server_cancel(kf_server_t *srv, int64_t job_id);
 kf_status_t kf_server_destroy(kf_server_t *srv);
 
 /* RTS smoother that allocates no device memory.
@@ -443,6 +450,28 @@ kf_status_t kf_autotune(kf_op_t op, const kf_model_t *model, int64_t T, const vo
                         void *m_out, void *P_out, int reps, void *workspace, void *stream);
 kf_status_t kf_tuning_get(kf_op_t op, int nx, int ny, kf_precision_t prec, int64_t T, int *scan, int *threads,
                           int *lookback_warps, int *steps_per_thread, double *ms);
+/* Batch autotuner.  kf_autotune_batch times kf_batch_smooth on the caller's
+ * batch (same arguments as kf_batch_smooth, no log-likelihoods; outputs are
+ * overwritten) for 1, 2 or 4 look-back warps of the 128-thread CTA and
+ * three steps-per-thread settings (the library's choice, about half and
+ * about twice one wave of resident tiles), median of reps runs each after
+ * one warm-up, and records the fastest for (op, nx, ny, precision,
+ * floor(log2 total steps)) with nx, ny those of models[0].  Later
+ * kf_batch_smooth calls (and the server's batches) whose batch has that key
+ * use it, unless KF_OPT_LOOKBACK_WARPS or KF_OPT_POSITIONS_PER_THREAD is set.
+ * Synchronous; kf_timing_enable must be off.  The entries share the table
+ * (and the file of kf_tuning_save) with the one-sequence entries, under op
+ * code op + 8.  kf_batch_tuning_get reads an entry (KF_ERR_ARG if none). */
+kf_status_t kf_autotune_batch(kf_op_t op, const kf_model_t *models, int nmodels, const int32_t *model_of_seq, int nseq,
+                              const int64_t *offsets, const void *y, kf_precision_t prec, void *m_out, void *P_out,
+                              int reps, void *workspace, void *stream);
+kf_status_t kf_batch_tuning_get(kf_op_t op, int nx, int ny, kf_precision_t prec, int64_t total_steps,
+                                int *lookback_warps, int *steps_per_thread, double *ms);
+/* The launch request of the calling thread's last one-sequence or batched
+ * call, after the KF_OPT_* options and the tuning table were applied: the
+ * scan (kf_scan_t), threads per CTA, look-back warps and steps per thread,
+ * each 0 where the library chooses.  All zero before the first call. */
+kf_status_t kf_last_launch_config(int *scan, int *threads, int *lookback_warps, int *steps_per_thread);
 kf_status_t kf_tuning_save(const char *path);
 kf_status_t kf_tuning_load(const char *path);
 kf_status_t kf_tuning_clear(void);

@@ -29,7 +29,8 @@ SCANS = {"auto": 0, "dlb": 1, "decoupled_lookback": 1, "hillis_steele": 2, "hs":
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_fp64solve": 2, "mixed": 2}
 OPS = {"filter": 0, "rts": 1, "two_filter": 2, "tf": 2}
 STATUS = {0: "KF_OK", 1: "KF_ERR_ARG", 2: "KF_ERR_NOT_PD", 3: "KF_ERR_CUDA", 4: "KF_ERR_OOM",
-          5: "KF_ERR_TIMEOUT", 6: "KF_ERR_BUDGET", 7: "KF_ERR_BUSY", 8: "KF_ERR_CAPACITY"}
+          5: "KF_ERR_TIMEOUT", 6: "KF_ERR_BUDGET", 7: "KF_ERR_BUSY", 8: "KF_ERR_CAPACITY",
+          9: "KF_ERR_CANCELLED"}
 OPTIONS = {"wait_timeout_ns": 0, "test_skip_tile": 1, "positions_per_thread": 2, "threads": 3, "general_solve": 4,
            "lookback_warps": 5, "sengupta_n": 6, "filter_kernel": 7,
            "rts_kernel": 8}
@@ -90,7 +91,11 @@ def lib():
         L.kf_tuning_get.argtypes = [i, i, i, i, i64, IP, IP, IP, IP, ctypes.POINTER(ctypes.c_double)]
         L.kf_tuning_save.argtypes = [ctypes.c_char_p]
         L.kf_tuning_load.argtypes = [ctypes.c_char_p]
-        for f in ("kf_autotune", "kf_tuning_get", "kf_tuning_save", "kf_tuning_load", "kf_tuning_clear"):
+        L.kf_autotune_batch.argtypes = [i, MP, i, vp, i, vp, vp, i, vp, vp, i, vp, vp]
+        L.kf_batch_tuning_get.argtypes = [i, i, i, i, i64, IP, IP, ctypes.POINTER(ctypes.c_double)]
+        L.kf_last_launch_config.argtypes = [IP, IP, IP, IP]
+        for f in ("kf_autotune", "kf_tuning_get", "kf_tuning_save", "kf_tuning_load", "kf_tuning_clear",
+                  "kf_autotune_batch", "kf_batch_tuning_get", "kf_last_launch_config"):
             getattr(L, f).restype = ctypes.c_int
         L.kf_rts_smooth_noalloc.argtypes = [MP, i64, vp, i, vp, vp, vp, vp, vp]
         L.kf_batch_smooth.argtypes = [i, MP, i, vp, i, vp, vp, i, vp, vp, vp, vp, vp]
@@ -112,8 +117,9 @@ def lib():
         L.kf_server_wait.argtypes = [vp, i64, ctypes.c_double]
         L.kf_server_release.argtypes = [vp, i64]
         L.kf_server_destroy.argtypes = [vp]
+        L.kf_server_cancel.argtypes = [vp, i64]
         for f in ("kf_server_create", "kf_server_submit", "kf_server_poll", "kf_server_wait", "kf_server_release",
-                  "kf_server_destroy"):
+                  "kf_server_destroy", "kf_server_cancel"):
             getattr(L, f).restype = ctypes.c_int
         L.kf_rts_smooth_noalloc.restype = ctypes.c_int
         L.kf_trace_phases.restype = ctypes.c_int
@@ -566,6 +572,15 @@ class Server:
     def wait(self, jid, timeout_s=60.0):
         _check(lib().kf_server_wait(self.h, int(jid), float(timeout_s)), "kf_server_wait")
 
+    def cancel(self, jid):
+        """Take a queued job out of the queue (True), or False when it has
+        started or finished already (kf_server_cancel)."""
+        rc = lib().kf_server_cancel(self.h, int(jid))
+        if rc == 7:   # KF_ERR_BUSY
+            return False
+        _check(rc, "kf_server_cancel")
+        return True
+
     def release(self, jid):
         _check(lib().kf_server_release(self.h, int(jid)), "kf_server_release")
         self._keep.pop(jid, None)
@@ -608,6 +623,38 @@ def kf_tuning_get(op, nx, ny, precision, T):
         return None
     return {"scan": SCAN_NAMES[v[0].value], "threads": v[1].value, "lookback_warps": v[2].value,
             "steps_per_thread": v[3].value, "ms": ms.value}
+
+
+def kf_autotune_batch(op, models, offsets, y, precision="fp32", model_of=None, reps=5, workspace=None,
+                      stream=None):
+    """Time kf_batch_smooth's candidate configurations on this batch and
+    record the fastest (see kfscan.h).  Returns the recorded entry."""
+    ms, arr, offs, nseq, mof, m_out, P_out, _ = _batch_args(models, offsets, y, precision, model_of, None, None,
+                                                            False)
+    rc = lib().kf_autotune_batch(OPS[op], arr, len(ms), None if mof is None else mof.ctypes.data_as(ctypes.c_void_p),
+                                 nseq, offs.ctypes.data_as(ctypes.c_void_p), _ptr(y), PRECISIONS[precision],
+                                 _ptr(m_out), _ptr(P_out), int(reps), _ptr(workspace), _stream(stream))
+    _check(rc, "kf_autotune_batch")
+    return kf_batch_tuning_get(op, ms[0].nx, ms[0].ny, precision, int(offs[-1]))
+
+
+def kf_batch_tuning_get(op, nx, ny, precision, total_steps):
+    v = [ctypes.c_int(0) for _ in range(2)]
+    t = ctypes.c_double(0)
+    rc = lib().kf_batch_tuning_get(OPS[op], nx, ny, PRECISIONS[precision], int(total_steps),
+                                   *[ctypes.byref(x) for x in v], ctypes.byref(t))
+    if rc != 0:
+        return None
+    return {"lookback_warps": v[0].value, "steps_per_thread": v[1].value, "ms": t.value}
+
+
+def kf_last_launch_config():
+    """The calling thread's last launch request (see kfscan.h): a dict of
+    scan, threads, lookback_warps and steps_per_thread (0 = library's choice)."""
+    v = [ctypes.c_int(0) for _ in range(4)]
+    _check(lib().kf_last_launch_config(*[ctypes.byref(x) for x in v]), "kf_last_launch_config")
+    return {"scan": v[0].value, "threads": v[1].value, "lookback_warps": v[2].value,
+            "steps_per_thread": v[3].value}
 
 
 def kf_tuning_save(path):

@@ -586,10 +586,26 @@ struct TuneCfg {
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneCfg> g_tune;
 
+// Batched launches (kf_batch_smooth, the server's batches) keep their entries
+// under op + KF_TUNE_BATCH, keyed by the batch's total number of steps.
+constexpr int KF_TUNE_BATCH = 8;
+
 static int floor_log2(int64_t T) {
     int l = 0;
     while ((int64_t(2) << l) <= T) ++l;
     return l;
+}
+
+// The launch request of this thread's last call, after the options and the
+// tuning table were applied (0 = the library's own choice); see
+// kf_last_launch_config.
+static thread_local int t_last_cfg[4] = {0, 0, 0, 0};
+
+static void note_launch(int scan, int threads, int lbw, int k) {
+    t_last_cfg[0] = scan;
+    t_last_cfg[1] = threads;
+    t_last_cfg[2] = lbw;
+    t_last_cfg[3] = k;
 }
 
 static bool tuned(int op, int nx, int ny, int prec, int64_t T, TuneCfg *c) {
@@ -657,6 +673,7 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
         if (q.lookback_warps == 0) q.lookback_warps = tc.lookback_warps;
         if (q.k_override == 0) q.k_override = tc.k;
     }
+    note_launch(q.scan, q.threads, q.lookback_warps, q.k_override);
     s = device_status_word(&q.status);
     KF_DBG("status word %p (%d)\n", (void *)q.status, int(s));
     if (s != KF_OK) return s;
@@ -781,6 +798,15 @@ static kf_status_t run_batch(kf_op_t op, const kf_model_t *models, int nmodels, 
         q.threads = int(g_opt[KF_OPT_THREADS].load());
         q.no_lowrank = int(g_opt[KF_OPT_GENERAL_SOLVE].load());
         q.lookback_warps = int(g_opt[KF_OPT_LOOKBACK_WARPS].load());
+        // the autotuner's entry for batches of this class and size, when the
+        // launch options are at their defaults
+        TuneCfg tc;
+        if (q.threads == 0 && q.lookback_warps == 0 && q.k_override == 0 &&
+            tuned(KF_TUNE_BATCH + int(op), nx, ny, int(prec), total, &tc)) {
+            q.lookback_warps = tc.lookback_warps;
+            q.k_override = tc.k;
+        }
+        note_launch(KF_SCAN_DLB_I, 128, q.lookback_warps, q.k_override);
         s = device_status_word(&q.status);
     }
     if (s == KF_OK) {
@@ -907,6 +933,7 @@ const char *kf_status_string(kf_status_t s) {
         case KF_ERR_BUDGET: return "job exceeds the device memory budget";
         case KF_ERR_BUSY: return "queue full or unknown job";
         case KF_ERR_CAPACITY: return "request exceeds a fixed scratch capacity";
+        case KF_ERR_CANCELLED: return "job cancelled before it started";
     }
     return "unknown status";
 }
@@ -1218,6 +1245,91 @@ kf_status_t kf_autotune(kf_op_t op, const kf_model_t *model, int64_t T, const vo
     if (kf_sync_status(stream) != KF_OK) return KF_ERR_TIMEOUT;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[TuneKey{int(op), model->nx, model->ny, int(prec), floor_log2(T)}] = best;
+    return KF_OK;
+}
+
+kf_status_t kf_autotune_batch(kf_op_t op, const kf_model_t *models, int nmodels, const int32_t *model_of_seq, int nseq,
+                              const int64_t *offsets, const void *y, kf_precision_t prec, void *m_out, void *P_out,
+                              int reps, void *workspace, void *stream) {
+    if (!models || nmodels < 1 || nseq < 1 || !offsets || !y || !m_out || reps < 1 || reps > 1000)
+        return KF_ERR_ARG;
+    if (op != KF_OP_FILTER && !P_out) return KF_ERR_ARG;
+    if (op != KF_OP_FILTER && op != KF_OP_RTS && op != KF_OP_TWO_FILTER) return KF_ERR_ARG;
+    if (timing_on()) return KF_ERR_ARG;
+    const int64_t total = offsets[nseq];
+    if (total < 1) return KF_ERR_ARG;
+    // candidates: look-back warps of the 128-thread CTA, and the steps per
+    // thread (one wave of resident tiles, half and double that)
+    std::vector<TuneCfg> cands;
+    for (int lb = 1; lb <= 4; lb *= 2)
+        for (int kscale = 0; kscale < 3; ++kscale) {
+            int k = 0;
+            if (kscale > 0) {
+                const int64_t per = (total + int64_t(152) * 128 - 1) / (int64_t(152) * 128);
+                k = int(kscale == 1 ? (per + 1) / 2 : per * 2);
+                if (k < 1) k = 1;
+            }
+            cands.push_back(TuneCfg{KF_SCAN_DLB_I, 128, lb, k, 0});
+        }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KF_ERR_CUDA;
+    const int64_t saved[3] = {g_opt[KF_OPT_THREADS].load(), g_opt[KF_OPT_LOOKBACK_WARPS].load(),
+                              g_opt[KF_OPT_POSITIONS_PER_THREAD].load()};
+    TuneCfg best{KF_SCAN_DLB_I, 128, 0, 0, 1e30};
+    kf_status_t s = KF_OK;
+    for (TuneCfg c : cands) {
+        g_opt[KF_OPT_THREADS].store(0);
+        g_opt[KF_OPT_LOOKBACK_WARPS].store(c.lookback_warps);
+        g_opt[KF_OPT_POSITIONS_PER_THREAD].store(c.k);
+        auto call = [&]() {
+            return kf_batch_smooth(op, models, nmodels, model_of_seq, nseq, offsets, y, prec, m_out, P_out, nullptr,
+                                   workspace, stream);
+        };
+        s = call();   // warm-up
+        if (s != KF_OK) break;
+        std::vector<float> ts;
+        for (int r = 0; r < reps && s == KF_OK; ++r) {
+            cudaEventRecord(e0, st);
+            s = call();
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) s = KF_ERR_CUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ts.push_back(ms);
+        }
+        if (s != KF_OK) break;
+        std::sort(ts.begin(), ts.end());
+        c.ms = ts[ts.size() / 2];
+        if (c.ms < best.ms) best = c;
+    }
+    g_opt[KF_OPT_THREADS].store(saved[0]);
+    g_opt[KF_OPT_LOOKBACK_WARPS].store(saved[1]);
+    g_opt[KF_OPT_POSITIONS_PER_THREAD].store(saved[2]);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != KF_OK) return s;
+    if (kf_sync_status(stream) != KF_OK) return KF_ERR_TIMEOUT;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[TuneKey{KF_TUNE_BATCH + int(op), models[0].nx, models[0].ny, int(prec), floor_log2(total)}] = best;
+    return KF_OK;
+}
+
+kf_status_t kf_batch_tuning_get(kf_op_t op, int nx, int ny, kf_precision_t prec, int64_t total_steps,
+                                int *lookback_warps, int *steps_per_thread, double *ms) {
+    TuneCfg c;
+    if (!tuned(KF_TUNE_BATCH + int(op), nx, ny, int(prec), total_steps, &c)) return KF_ERR_ARG;
+    if (lookback_warps) *lookback_warps = c.lookback_warps;
+    if (steps_per_thread) *steps_per_thread = c.k;
+    if (ms) *ms = c.ms;
+    return KF_OK;
+}
+
+kf_status_t kf_last_launch_config(int *scan, int *threads, int *lookback_warps, int *steps_per_thread) {
+    if (scan) *scan = t_last_cfg[0];
+    if (threads) *threads = t_last_cfg[1];
+    if (lookback_warps) *lookback_warps = t_last_cfg[2];
+    if (steps_per_thread) *steps_per_thread = t_last_cfg[3];
     return KF_OK;
 }
 

@@ -380,6 +380,25 @@ kf_status_t kf_server_release(kf_server_t *srv, int64_t job_id) {
     return KF_OK;
 }
 
+kf_status_t kf_server_cancel(kf_server_t *srv, int64_t job_id) {
+    if (!srv) return KF_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto it = srv->jobs.find(job_id);
+        if (it == srv->jobs.end()) return KF_ERR_BUSY;
+        Job *j = it->second;
+        auto q = std::find(srv->queue.begin(), srv->queue.end(), j);
+        if (j->done || q == srv->queue.end()) return KF_ERR_BUSY;   // running or finished
+        srv->queue.erase(q);
+        j->status = KF_ERR_CANCELLED;
+        j->t_done = now_s();
+        j->done = true;
+    }
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_one();
+    return KF_OK;
+}
+
 kf_status_t kf_server_destroy(kf_server_t *srv) {
     if (!srv) return KF_ERR_ARG;
     {

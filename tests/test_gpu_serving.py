@@ -84,3 +84,45 @@ def test_budget_rejection():
         assert e.value.status == 6          # KF_ERR_BUDGET
     finally:
         srv.close()
+
+
+def test_cancel_a_queued_job():
+    """A job still waiting in the queue (the server's only stream is busy with
+    a long job of another class) is cancelled: it is done with
+    KF_ERR_CANCELLED and its outputs are untouched; the running job is not
+    affected; cancelling a finished or unknown job reports that it cannot."""
+    import time
+    import torch
+    import paper_2511_10363_gb300 as kf
+    big = W.cv_model()
+    Tb = 1 << 21
+    yb = torch.tensor(W.simulate(big, Tb, seed=77)).pin_memory()
+    mb = torch.empty((Tb, 4), dtype=torch.float64).pin_memory()
+    Pb = torch.empty((Tb, 4, 4), dtype=torch.float64).pin_memory()
+    small = W.model_for_nx(2, seed=2)
+    Ts = 500
+    ys = torch.tensor(W.simulate(small, Ts, seed=78).astype(np.float32)).pin_memory()
+    ms = torch.full((Ts, 2), float("nan"), dtype=torch.float32).pin_memory()
+    srv = kf.Server(budget_bytes=2 << 30, max_inflight=1, max_batch_steps=1 << 23)
+    try:
+        j1 = srv.submit("rts", big, yb, "fp64", mb, Pb, None)
+        t0 = time.time()
+        while srv.poll(j1)[1][1] == 0.0 and not srv.poll(j1)[0]:   # until its batch has started
+            assert time.time() - t0 < 60
+            time.sleep(0.0005)
+        j2 = srv.submit("filter", small, ys, "fp32", ms, None, None)
+        assert srv.cancel(j2)
+        with pytest.raises(kf.KfError) as e:
+            srv.poll(j2)
+        assert e.value.status == 9                 # KF_ERR_CANCELLED
+        with pytest.raises(kf.KfError):
+            srv.wait(j2, 10)
+        srv.wait(j1, 120)
+        assert not srv.cancel(j1)                  # finished
+        assert not srv.cancel(123456789)           # unknown
+        assert torch.isnan(ms).all()               # never written
+        mf, Pf, _ = oracle.kf(big, yb.numpy())
+        msr, Psr = oracle.rts(big, mf, Pf)
+        assert mean_err(mb.numpy(), msr, Psr) < 1e-9 and cov_err(Pb.numpy(), Psr) < 1e-9
+    finally:
+        srv.close()
