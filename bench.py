@@ -411,6 +411,56 @@ def workload_sweep(args):
                       "timing": "median of 10 after 2 dropped runs (CUDA events)", "results": out}))
 
 
+def workload_tune(args):
+    """Regenerates the GB300 tuning table: kf_autotune for the filter, the
+    RTS and the two-filter smoother at nx 2, 4, 8 (ny = nx / 2), every
+    precision, T = 2^10 .. 2^22, and kf_autotune_batch for ragged batches
+    (lengths log-uniform in [64, 65536]) of 2^10 .. 2^25 total steps, written
+    to --save-tuning (default: the shipped table)."""
+    import time as _t
+    import torch
+    import paper_2511_10363_gb300 as kf
+    path = args.save_tuning or TUNING_TABLE
+    kf.kf_tuning_clear()
+    t0 = _t.time()
+    n_one = n_batch = 0
+    for nx in (2, 4, 8):
+        ny = nx // 2
+        model = W.cv_model() if nx == 4 else W.model_for_nx(nx, seed=nx)
+        emax = 22 if nx <= 4 else 21
+        y64 = W.simulate(model, 1 << emax, seed=3)
+        for prec in ("fp32", "fp64", "fp32_fp64solve"):
+            dt = kf.dtype_of(prec)
+            yall = torch.tensor(y64, dtype=dt, device="cuda")
+            for op in ("filter", "rts", "tf"):
+                for e in range(10, emax + 1):
+                    T = 1 << e
+                    ws = torch.empty(kf.kf_workspace_size(op, nx, ny, T, prec, "auto"), dtype=torch.uint8,
+                                     device="cuda")
+                    kf.kf_autotune(op, model, yall[:T].contiguous(), prec, reps=3, workspace=ws)
+                    n_one += 1
+                    del ws
+            del yall
+    for nx in (2, 4, 8):
+        model = W.cv_model() if nx == 4 else W.model_for_nx(nx, seed=nx)
+        for e in range(10, 26):
+            # a ragged batch whose total lies in [2^e, 2^(e+1))
+            lengths = W.loguniform_lengths(8 + (1 << max(0, e - 8)), 64, 65536, seed=e)
+            lengths = lengths[np.cumsum(lengths) <= int(1.5 * (1 << e))]
+            if lengths.size == 0 or lengths.sum() < (1 << e):
+                lengths = np.array([int(1.5 * (1 << e))], dtype=np.int64)
+            y, offs = W.ragged_batch(model, lengths, seed=e)
+            for prec in (("fp32", "fp64", "fp32_fp64solve") if nx == 4 else ("fp32",)):
+                yt = torch.tensor(y, dtype=kf.dtype_of(prec), device="cuda")
+                for op in ("filter", "rts", "tf"):
+                    kf.kf_autotune_batch(op, [model], offs, yt, prec, reps=3)
+                    n_batch += 1
+                del yt
+    kf.kf_tuning_save(path)
+    print(json.dumps({"workload": "tune", "table": os.path.relpath(path, ROOT), "one_sequence_entries": n_one,
+                      "batch_entries": n_batch, "seconds": round(_t.time() - t0, 1)}))
+
+
 def errors_vs_reference(m, P, ll, mref, Pref, llref):
     """Per-output errors: normwise per step (max over steps) and elementwise
     with an absolute floor of 1e-12 * max |x|."""
@@ -766,7 +816,7 @@ def main():
     ap.add_argument("--retune", action="store_true", help="autotune even when the tuning table has an entry")
     ap.add_argument("--save-tuning", default=None, help="write the tuning table after autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "sweep", "mixed", "batch", "serving", "tv"],
+    ap.add_argument("--workload", default="single", choices=["single", "sweep", "mixed", "batch", "serving", "tv", "tune"],
                     help="single: the headline line (default); the others print their own line")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: arrival window (s)")
@@ -791,7 +841,7 @@ def main():
         torch.cuda.set_device(local)
         kbuild.build()
         {"sweep": workload_sweep, "mixed": workload_mixed, "batch": workload_batch,
-         "serving": workload_serving, "tv": workload_tv}[args.workload](args)
+         "serving": workload_serving, "tv": workload_tv, "tune": workload_tune}[args.workload](args)
         return
 
     import torch
