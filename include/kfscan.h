@@ -375,6 +375,21 @@ kf_status_t kf_stream_status(void *stream);
  *                               sequence (nx 2 or 4, the decoupled look-back
  *                               scan) runs its dedicated kernel; 1: the
  *                               generic look-back kernel.
+ *   KF_OPT_COVARIANCE_TABLES    0 (default): kf_filter and kf_rts_smooth on
+ *                               a time-invariant model with ny = nx / 2
+ *                               (nx 2, 4 or 8, any precision, the decoupled
+ *                               look-back scan, KF_OPT_FILTER_KERNEL and
+ *                               KF_OPT_RTS_KERNEL at 0) take the
+ *                               data-independent halves of the elements --
+ *                               filtering covariances, gains, smoothed
+ *                               covariances -- from FP64 tables the host
+ *                               computes once per model (the covariance
+ *                               recursion to its fixed point, relative change
+ *                               below 2^-46), and scan only the means on the
+ *                               device; the smoother needs T >= k0 + kb + 1
+ *                               (the lengths of the two transients, a few
+ *                               hundred steps for a well-damped model).
+ *                               1: the per-step kernels above.
  * Returns KF_ERR_ARG for an unknown option or a value out of range. */
 typedef enum {
     KF_OPT_WAIT_TIMEOUT_NS = 0,
@@ -385,7 +400,8 @@ typedef enum {
     KF_OPT_LOOKBACK_WARPS = 5,
     KF_OPT_SENGUPTA_N = 6,
     KF_OPT_FILTER_KERNEL = 7,
-    KF_OPT_RTS_KERNEL = 8
+    KF_OPT_RTS_KERNEL = 8,
+    KF_OPT_COVARIANCE_TABLES = 9
 } kf_option_t;
 kf_status_t kf_set_option(kf_option_t opt, int64_t value);
 int64_t kf_get_option(kf_option_t opt); /* -1 for an unknown option */
@@ -467,6 +483,18 @@ kf_status_t kf_autotune_batch(kf_op_t op, const kf_model_t *models, int nmodels,
                               int reps, void *workspace, void *stream);
 kf_status_t kf_batch_tuning_get(kf_op_t op, int nx, int ny, kf_precision_t prec, int64_t total_steps,
                                 int *lookback_warps, int *steps_per_thread, double *ms);
+/* The covariance tables of a time-invariant model with ny = nx / 2 (nx 2,
+ * 4 or 8; see KF_OPT_COVARIANCE_TABLES): k0 (the times 1..k0 whose
+ * filtering covariance has not yet settled), kb (the times T - kb + 1 .. T
+ * whose smoothed covariance has not), and the settled filtering covariance
+ * P_inf (nx x nx), gain K_inf (nx x ny), RTS gain E_inf (nx x nx) and
+ * smoothed covariance Ps_inf (nx x nx), row-major into host buffers (any
+ * may be NULL).  Host only; KF_ERR_ARG when the tables do not apply (the
+ * recursion does not settle within 2^16 steps, or a covariance is not
+ * positive definite). */
+kf_status_t kf_covariance_tables(const kf_model_t *model, int *k0, int *kb, double *P_inf, double *K_inf,
+                                 double *E_inf, double *Ps_inf);
+
 /* The launch request of the calling thread's last one-sequence or batched
  * call, after the KF_OPT_* options and the tuning table were applied: the
  * scan (kf_scan_t), threads per CTA, look-back warps and steps per thread,

@@ -33,7 +33,7 @@ STATUS = {0: "KF_OK", 1: "KF_ERR_ARG", 2: "KF_ERR_NOT_PD", 3: "KF_ERR_CUDA", 4: 
           9: "KF_ERR_CANCELLED"}
 OPTIONS = {"wait_timeout_ns": 0, "test_skip_tile": 1, "positions_per_thread": 2, "threads": 3, "general_solve": 4,
            "lookback_warps": 5, "sengupta_n": 6, "filter_kernel": 7,
-           "rts_kernel": 8}
+           "rts_kernel": 8, "covariance_tables": 9}
 
 _lib = None
 
@@ -94,6 +94,9 @@ def lib():
         L.kf_autotune_batch.argtypes = [i, MP, i, vp, i, vp, vp, i, vp, vp, i, vp, vp]
         L.kf_batch_tuning_get.argtypes = [i, i, i, i, i64, IP, IP, ctypes.POINTER(ctypes.c_double)]
         L.kf_last_launch_config.argtypes = [IP, IP, IP, IP]
+        DP = ctypes.POINTER(ctypes.c_double)
+        L.kf_covariance_tables.argtypes = [MP, IP, IP, DP, DP, DP, DP]
+        L.kf_covariance_tables.restype = ctypes.c_int
         for f in ("kf_autotune", "kf_tuning_get", "kf_tuning_save", "kf_tuning_load", "kf_tuning_clear",
                   "kf_autotune_batch", "kf_batch_tuning_get", "kf_last_launch_config"):
             getattr(L, f).restype = ctypes.c_int
@@ -646,6 +649,25 @@ def kf_batch_tuning_get(op, nx, ny, precision, total_steps):
     if rc != 0:
         return None
     return {"lookback_warps": v[0].value, "steps_per_thread": v[1].value, "ms": t.value}
+
+
+def kf_covariance_tables(model):
+    """The covariance tables of a time-invariant model (see kfscan.h): a dict
+    of k0, kb and the settled P_inf, K_inf, E_inf, Ps_inf, or None when the
+    tables do not apply.  Host only."""
+    import numpy as np
+    m = _as_model(model)
+    n, ny = m.nx, m.ny
+    k0, kb = ctypes.c_int(0), ctypes.c_int(0)
+    out = {k: np.zeros(s) for k, s in (("P_inf", (n, n)), ("K_inf", (n, ny)), ("E_inf", (n, n)),
+                                        ("Ps_inf", (n, n)))}
+    ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    rc = lib().kf_covariance_tables(ctypes.byref(m.c), ctypes.byref(k0), ctypes.byref(kb), ptr(out["P_inf"]),
+                                    ptr(out["K_inf"]), ptr(out["E_inf"]), ptr(out["Ps_inf"]))
+    if rc != 0:
+        return None
+    out["k0"], out["kb"] = k0.value, kb.value
+    return out
 
 
 def kf_last_launch_config():

@@ -18,7 +18,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "_build", "libkfscan.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = (["kf_api.cu", "kf_serve.cu", "kf_n4_f32_t256.cu", "kf_tv_n2.cu", "kf_tv_n4.cu", "kf_tv_n8.cu",
-          "ti_n4_f32.cu", "ti_n2_f32.cu", "ti_n4_f64.cu", "ti_n2_f64.cu", "flop_count.cpp"]
+          "ti_n4_f32.cu", "ti_n2_f32.cu", "ti_n4_f64.cu", "ti_n2_f64.cu", "flop_count.cpp",
+          "gain_tables.cpp"]
+         + ["gs_n%d_%s.cu" % (n, p) for n in (8, 4, 2) for p in ("f64", "f32")]
          + ["kf_n%d_%s.cu" % (n, p) for n in (8, 4, 2) for p in ("f64", "mix", "f32")]
          + ["kf_n%d_%s_batch.cu" % (n, p) for n, p in ((8, "f64"), (8, "mix"), (8, "f32"), (4, "f64"), (4, "mix"))])
 

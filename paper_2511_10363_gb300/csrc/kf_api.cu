@@ -12,10 +12,12 @@
 
 #include <atomic>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <vector>
 
 #include "../../include/kfscan.h"
+#include "gain_tables.h"
 #include "kf_host.h"
 #include "kf_tv_host.h"
 
@@ -234,7 +236,7 @@ static std::mutex g_mu;
 static void *g_ws[64];
 static size_t g_ws_bytes[64];
 static int *g_status[64];
-static std::atomic<int64_t> g_opt[9] = {1000000000LL, -1, 0, 0, 0, 0, 1, 0, 0};   // KF_OPT_* by index
+static std::atomic<int64_t> g_opt[10] = {1000000000LL, -1, 0, 0, 0, 0, 1, 0, 0, 0};   // KF_OPT_* by index
 
 // KFSCAN_DEBUG=1 in the environment logs each stage of a call to stderr.
 bool debug_on() {
@@ -616,6 +618,44 @@ static bool tuned(int op, int nx, int ny, int prec, int64_t T, TuneCfg *c) {
     return true;
 }
 
+// Covariance tables of the models seen last (gain_tables.h), built once per
+// model; null for a model whose tables do not apply.
+static std::shared_ptr<const GainModel> gain_model_for(const kf_model_t *md) {
+    static std::mutex mu;
+    static std::vector<std::pair<uint64_t, std::shared_ptr<const GainModel>>> cache;   // most recent last
+    const int n = md->nx, m = md->ny;
+    uint64_t key = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t bytes) {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < bytes; ++i) key = (key ^ c[i]) * 1099511628211ull;
+    };
+    mix(&n, sizeof(n));
+    mix(&m, sizeof(m));
+    mix(md->F, sizeof(double) * n * n);
+    mix(md->Q, sizeof(double) * n * n);
+    mix(md->H, sizeof(double) * m * n);
+    mix(md->R, sizeof(double) * m * m);
+    mix(md->m0, sizeof(double) * n);
+    mix(md->P0, sizeof(double) * n * n);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto &e : cache)
+            if (e.first == key) return e.second;
+    }
+    std::shared_ptr<const GainModel> g;
+    {
+        auto b = std::make_shared<GainModel>();
+        if (gain_model_build(n, m, md->F, md->Q, md->H, md->R, md->m0, md->P0, b.get()) == 0) {
+            b->key = key;
+            g = b;
+        }
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    cache.emplace_back(key, g);
+    if (cache.size() > 16) cache.erase(cache.begin());
+    return g;
+}
+
 static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, kf_precision_t prec,
                        kf_scan_t scan, void *m1, void *P1, void *m2, void *P2, double *loglik, void *workspace,
                        void *stream) {
@@ -666,8 +706,17 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
     q.sg_n = g_opt[KF_OPT_SENGUPTA_N].load();
     q.filter_kernel = int(g_opt[KF_OPT_FILTER_KERNEL].load());
     q.rts_kernel = int(g_opt[KF_OPT_RTS_KERNEL].load());
-    TuneCfg tc;
-    if (scan == KF_SCAN_AUTO && tuned(op, md->nx, md->ny, q.prec, T, &tc)) {
+    // covariance tables of a time-invariant model (the per-step kernels when
+    // the tables do not apply)
+    std::shared_ptr<const GainModel> gm;
+    if ((op == KF_OP_FILTER_I || op == KF_OP_RTS_I) && g_opt[KF_OPT_COVARIANCE_TABLES].load() == 0 &&
+        q.filter_kernel == 0 && q.rts_kernel == 0 && md->ny * 2 == md->nx &&
+        (md->nx == 2 || md->nx == 4 || md->nx == 8)) {
+        gm = gain_model_for(md);
+        q.gain = gm.get();
+    }
+    TuneCfg tc;   // (calls on the covariance tables plan their own tiles)
+    if (scan == KF_SCAN_AUTO && !q.gain && tuned(op, md->nx, md->ny, q.prec, T, &tc)) {
         q.scan = tc.scan;
         if (q.threads == 0) q.threads = tc.threads;
         if (q.lookback_warps == 0) q.lookback_warps = tc.lookback_warps;
@@ -1325,6 +1374,23 @@ kf_status_t kf_batch_tuning_get(kf_op_t op, int nx, int ny, kf_precision_t prec,
     return KF_OK;
 }
 
+kf_status_t kf_covariance_tables(const kf_model_t *model, int *k0, int *kb, double *P_inf, double *K_inf,
+                                 double *E_inf, double *Ps_inf) {
+    kf_status_t s = check_model(model);
+    if (s != KF_OK) return s;
+    const int n = model->nx, m = model->ny;
+    if (m * 2 != n || (n != 2 && n != 4 && n != 8)) return KF_ERR_ARG;
+    std::shared_ptr<const GainModel> g = gain_model_for(model);
+    if (!g) return KF_ERR_ARG;
+    if (k0) *k0 = g->k0;
+    if (kb) *kb = g->kb;
+    if (P_inf) memcpy(P_inf, g->Pi, sizeof(double) * n * n);
+    if (K_inf) memcpy(K_inf, g->Ki, sizeof(double) * n * m);
+    if (E_inf) memcpy(E_inf, g->Ei, sizeof(double) * n * n);
+    if (Ps_inf) memcpy(Ps_inf, g->Psi, sizeof(double) * n * n);
+    return KF_OK;
+}
+
 kf_status_t kf_last_launch_config(int *scan, int *threads, int *lookback_warps, int *steps_per_thread) {
     if (scan) *scan = t_last_cfg[0];
     if (threads) *threads = t_last_cfg[1];
@@ -1452,9 +1518,11 @@ kf_status_t kf_measure_fma_peak(int fp64, double *flops_per_second) {
 }
 
 kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_RTS_KERNEL) return KF_ERR_ARG;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_COVARIANCE_TABLES) return KF_ERR_ARG;
     if (opt == KF_OPT_GENERAL_SOLVE && value != 0 && value != 1) return KF_ERR_ARG;
-    if ((opt == KF_OPT_FILTER_KERNEL || opt == KF_OPT_RTS_KERNEL) && value != 0 && value != 1) return KF_ERR_ARG;
+    if ((opt == KF_OPT_FILTER_KERNEL || opt == KF_OPT_RTS_KERNEL || opt == KF_OPT_COVARIANCE_TABLES) && value != 0 &&
+        value != 1)
+        return KF_ERR_ARG;
     if (opt == KF_OPT_SENGUPTA_N && (value < 1 || value > (int64_t(1) << 30) || (value & (value - 1)) != 0))
         return KF_ERR_ARG;
     if (opt == KF_OPT_LOOKBACK_WARPS && (value < 0 || value > 32)) return KF_ERR_ARG;
@@ -1466,7 +1534,7 @@ kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
 }
 
 int64_t kf_get_option(kf_option_t opt) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_RTS_KERNEL) return -1;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_COVARIANCE_TABLES) return -1;
     return g_opt[opt].load();
 }
 

@@ -61,6 +61,7 @@ struct LaunchReq {
     int counters_zeroed; // the look-back counters of this pass were cleared already
     int filter_kernel;   // 0: the time-invariant table kernel where it applies, 1: the generic scan kernel
     int rts_kernel;      // 0: the dedicated one-sequence RTS kernel where it applies, 1: the generic scan kernel
+    const void *gain;    // covariance tables of a time-invariant model (GainModel), or null
 };
 
 // Device cache of tile-scan tables (kf_api.cu): a table is found by its key,

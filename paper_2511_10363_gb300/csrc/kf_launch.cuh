@@ -8,6 +8,7 @@
 #include <new>
 #include <stdio.h>
 
+#include "gain_tables.h"
 #include "scan_levels.cuh"
 
 namespace kfs {
@@ -421,7 +422,19 @@ static TilePlan plan_tiles(int64_t total, int threads, int window, int resident,
 //   frec   : filter records [T][FRec::SIZE] (smoothers)
 //   lv_a, lv_b : level-scan element buffers [ES][Tpad] (level algorithms)
 struct WsLayout {
-    size_t ctl_f, ctl_r, agg, incl, llpart, frec, lv_a, lv_b, total;
+    size_t ctl_f, ctl_r, agg, incl, llpart, gw, frec, lv_a, lv_b, total;
+    int64_t gw_tiles;   // warp-tiles the covariance-table path can publish per direction
+};
+
+// The covariance-table path (gain_launch.cuh): its counters, published
+// words (4 N sizeof(R) / 4 words of 8 bytes per warp-tile: both directions'
+// aggregate and inclusive values) and per-warp-tile log-likelihood sums, for
+// up to min(T / 32 + 2, 65536) warp-tiles.
+template <int N, typename R>
+struct GwLayout {
+    static constexpr int NWD = N * int(sizeof(R)) / 4, STRIDE = 4 * NWD;
+    static int64_t tiles(int64_t T) { return T / 32 + 2 < 65536 ? T / 32 + 2 : 65536; }
+    static size_t bytes(int64_t T) { return 256 + size_t(tiles(T)) * (STRIDE * 8 + 8); }
 };
 
 static inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -445,6 +458,8 @@ WsLayout ws_layout(int op, int scan, int64_t T) {
     L.agg = o; o += al256(size_t(KF_MAX_TILES) * ESP * sizeof(R));
     L.incl = o; o += al256(size_t(KF_MAX_TILES) * CS * sizeof(R));
     L.llpart = o; o += al256(size_t(KF_MAX_TILES) * sizeof(double));
+    L.gw_tiles = GwLayout<N, R>::tiles(T);
+    L.gw = o; o += al256(GwLayout<N, R>::bytes(T));
     L.frec = L.lv_a = L.lv_b = 0;
     if (op != KF_OP_FILTER_I) {
         L.frec = o; o += al256(size_t(T) * FRec<N, R>::SIZE * sizeof(R));
@@ -770,6 +785,18 @@ bool rts_pass_launch(const FiltParams<2, double> &, const LaunchReq &, const KfB
 bool rts_pass_launch(const FiltParams<4, double> &, const LaunchReq &, const KfBufs<double> &, char *,
                      const WsLayout &, cudaError_t *);
 
+// The filter (and RTS) passes of one sequence of a time-invariant model on
+// the covariance tables (gain_launch.cuh), one translation unit per (nx,
+// precision): false when the call does not qualify, with nothing enqueued.
+template <int N>
+struct NTag {};
+#define KF_DECL_GAIN(N, R) \
+    bool gain_launch(NTag<N>, const GainModel &, const LaunchReq &, const KfBufs<R> &, char *, const WsLayout &, \
+                     double *, cudaError_t *);
+KF_DECL_GAIN(2, float) KF_DECL_GAIN(4, float) KF_DECL_GAIN(8, float)
+KF_DECL_GAIN(2, double) KF_DECL_GAIN(4, double) KF_DECL_GAIN(8, double)
+#undef KF_DECL_GAIN
+
 // The forward pass with the general or the low-rank operator forms, through
 // the requested scan algorithm (DLB_ONLY: always the decoupled look-back scan).
 template <int N, typename R, int MODE, class Src, int THREADS, int V, bool DLB_ONLY>
@@ -827,6 +854,11 @@ static cudaError_t launch_typed(const LaunchReq &q) {
     fa.want_ll = q.loglik != nullptr;
     // low-rank filter path when ny = nx / 2
     const bool lowrank = q.hm->m == N / 2 && q.scan == KF_SCAN_DLB_I && !q.no_lowrank;
+    // a time-invariant model on the covariance tables (clears its own counters)
+    if (q.gain && q.scan == KF_SCAN_DLB_I && (q.op == KF_OP_FILTER_I || q.op == KF_OP_RTS_I)) {
+        cudaError_t eg = cudaSuccess;
+        if (gain_launch(NTag<N>{}, *static_cast<const GainModel *>(q.gain), q, buf, ws, L, q.loglik, &eg)) return eg;
+    }
     LaunchReq qz = q;   // two look-back passes: one memset clears both passes' counters
     if (q.scan == KF_SCAN_DLB_I && q.op != KF_OP_FILTER_I) {
         const cudaError_t ez = cudaMemsetAsync(ws + L.ctl_f, 0, L.agg - L.ctl_f, q.stream);

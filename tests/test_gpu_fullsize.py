@@ -13,12 +13,23 @@ from tests.gpu_util import TOL, mean_err, cov_err, oracle_inputs
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision,T", [("fp32", 1 << 20), ("fp64", 1 << 20), ("fp32", 1 << 22)])
-def test_bench_workload_full_size(precision, T):
+@pytest.mark.parametrize("precision,T,tables", [("fp32", 1 << 20, 0), ("fp64", 1 << 20, 0), ("fp32", 1 << 22, 0),
+                                                ("fp32", 1 << 20, 1), ("fp64", 1 << 20, 1)])
+def test_bench_workload_full_size(precision, T, tables):
+    """tables = 0: the default path (covariance tables for the RTS smoother,
+    per-step kernels for the two-filter smoother); 1: per-step kernels only."""
     import torch
     import paper_2511_10363_gb300 as kf
     from paper_2511_10363_gb300 import build
     build.build()
+    kf.kf_set_option("covariance_tables", tables)
+    try:
+        _full_size(kf, torch, precision, T)
+    finally:
+        kf.kf_set_option("covariance_tables", 0)
+
+
+def _full_size(kf, torch, precision, T):
     model = W.cv_model()
     y = oracle_inputs(W.simulate(model, T, seed=1), precision)
     mf, Pf, ll = oracle.kf(model, y)

@@ -55,14 +55,22 @@ def compare(op, model, y, precision, scan, loglik=True):
     return errs
 
 
+@pytest.mark.parametrize("tables", [0, 1])
 @pytest.mark.parametrize("op", ["filter", "rts", "tf"])
 @pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("nx", [2, 4, 8])
 @pytest.mark.parametrize("T", [1, 2, 3, 100, 1000, 4097])
-def test_dlb_parity(op, precision, nx, T):
+def test_dlb_parity(op, precision, nx, T, tables):
+    """tables = 0: the covariance-table path where it applies (the filter at
+    any T, the RTS smoother from T = k0 + kb + 1 on); 1: the per-step kernels."""
+    import paper_2511_10363_gb300 as kf
     model = model_for(nx, seed=nx * 7 + T % 5)
     y = W.simulate(model, T, seed=1000 + T)
-    compare(op, model, y, precision, "dlb")
+    kf.kf_set_option("covariance_tables", tables)
+    try:
+        compare(op, model, y, precision, "dlb")
+    finally:
+        kf.kf_set_option("covariance_tables", 0)
 
 
 @pytest.mark.parametrize("op", ["filter", "rts", "tf"])
@@ -92,20 +100,23 @@ def test_sengupta_threshold(N, T):
         kf.kf_set_option("sengupta_n", 1)
 
 
+@pytest.mark.parametrize("tables", [0, 1])
 @pytest.mark.parametrize("K", [1, 2, 3, 7])
 @pytest.mark.parametrize("op", ["filter", "rts", "tf"])
-def test_dlb_many_tiles(K, op):
+def test_dlb_many_tiles(K, op, tables):
     """Force K time steps per thread so that T = 5000 spans many tiles, and
     the look-back combines many predecessor aggregates."""
     import paper_2511_10363_gb300 as kf
     model = W.cv_model()
     y = W.simulate(model, 5000, seed=3000 + K)
     kf.kf_set_option("positions_per_thread", K)
+    kf.kf_set_option("covariance_tables", tables)
     try:
         compare(op, model, y, "fp64", "dlb")
         compare(op, model, y, "fp32", "dlb")
     finally:
         kf.kf_set_option("positions_per_thread", 0)
+        kf.kf_set_option("covariance_tables", 0)
 
 
 @pytest.mark.parametrize("nx,ny", [(2, 2), (4, 1), (4, 3), (8, 2), (8, 8), (2, 5)])
@@ -168,6 +179,7 @@ def test_fold_table(K, model_kind, threads):
     y = W.simulate(model, T, seed=500 + K)
     kf.kf_set_option("positions_per_thread", K)
     kf.kf_set_option("threads", threads)
+    kf.kf_set_option("covariance_tables", 1)   # the per-step kernels
     try:
         # the log-likelihood in FP64 only: in the working precision FP32 the
         # innovation of a long tracking sequence (positions ~1e7) cancels
@@ -177,3 +189,4 @@ def test_fold_table(K, model_kind, threads):
     finally:
         kf.kf_set_option("positions_per_thread", 0)
         kf.kf_set_option("threads", 0)
+        kf.kf_set_option("covariance_tables", 0)

@@ -22,7 +22,9 @@ def built():
     from paper_2511_10363_gb300 import build
     build.build()
     import paper_2511_10363_gb300 as kf
+    kf.kf_set_option("covariance_tables", 1)   # the per-step kernels
     yield
+    kf.kf_set_option("covariance_tables", 0)
     for k in ("positions_per_thread", "threads", "filter_kernel"):
         kf.kf_set_option(k, 0)
 
