@@ -94,6 +94,27 @@ def rts_step_flops(n):
     return rts_fold_flops(n) + rts_carry_flops(n)
 
 
+# Work model of the covariance-table path (time-invariant model, the
+# default for kf_filter / kf_rts_smooth): the device scans only the means,
+# s <- A s + B u, once in the fold and once in the replay of every step; the
+# covariances are written from tables.
+def gain_filter_flops(n, m, loglik=False):
+    f = 2 * 2 * (n * n + n * m)                 # fold and replay: A s + B y
+    if loglik:
+        f += 2 * m * n + m * (m + 1) + 2 * m    # y - H F s, W v, |W v|^2
+    return f
+
+
+def gain_rts_flops(n):
+    return 2 * 2 * (n * n + n * n)              # fold and replay: E s + G xbar
+
+
+def gain_step_bytes(n, m, w):
+    filt = (m + n) * w                          # read y, write the filter mean
+    rts = (n + n + n * n) * w                   # read it back, write smoothed mean + full covariance
+    return filt, rts
+
+
 def step_bytes(n, m, w):
     S = n * (n + 1) // 2
     filt = (m + n + S) * w                  # read y, write filter mean + packed cov
@@ -945,6 +966,40 @@ def main():
     kern_ms, kern, _ = timed_steps(True)              # the same steps with per-kernel events
     ck = clocks.stop()
 
+    # which path ran: the covariance tables of a time-invariant model (the
+    # default for the RTS smoother from T = k0 + kb + 1 on a look-back scan),
+    # else the per-step kernels; the per-step kernels are also timed on the
+    # same steps for reference
+    tabs = kf.kf_covariance_tables(model)
+    gain_path = (args.op == "rts" and args.scan in ("auto", "dlb") and tabs is not None
+                 and T >= tabs["k0"] + tabs["kb"] + 1)
+    path_note = ("covariance tables: filtering / smoothed covariances and gains from host FP64 tables "
+                 "(k0=%d, kb=%d transient steps), the device scans the means" % (tabs["k0"], tabs["kb"])
+                 if gain_path else "per-step kernels (every element built and combined on the device)")
+    per_step = None
+    if gain_path:
+        kf.kf_set_option("covariance_tables", 1)
+        try:
+            for _ in range(2):
+                step()
+            n_ps = max(3, min(args.steps, 10))
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n_ps)]
+            torch.cuda.synchronize()
+            for k in range(n_ps):
+                flush.zero_()
+                ev[2 * k].record()
+                step()
+                ev[2 * k + 1].record()
+            torch.cuda.synchronize()
+            if kf.kf_sync_status() != 0:
+                raise RuntimeError("kernel status in the per-step timing")
+            ps_ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(n_ps)) / n_ps
+            per_step = {"ms_per_step": ps_ms, "steps_per_s": T / (ps_ms * 1e-3),
+                        "note": "the same step with KF_OPT_COVARIANCE_TABLES=1 (every element built and "
+                                "combined on the device), %d steps" % n_ps}
+        finally:
+            kf.kf_set_option("covariance_tables", 0)
+
     max_ms = max_over_ranks(dist, total_ms, "cuda")
     value = job_rate(world, args.steps, T, max_ms)
 
@@ -995,9 +1050,14 @@ def main():
         return
 
     # ---- roofline of the dominant kernel
-    fb, rb = step_bytes(nx, ny, w)
-    f_flops = filter_step_flops(nx, ny, want_ll)
-    r_flops = rts_step_flops(nx)
+    if gain_path:
+        fb, rb = gain_step_bytes(nx, ny, w)
+        f_flops = gain_filter_flops(nx, ny, want_ll)
+        r_flops = gain_rts_flops(nx)
+    else:
+        fb, rb = step_bytes(nx, ny, w)
+        f_flops = filter_step_flops(nx, ny, want_ll)
+        r_flops = rts_step_flops(nx)
     fma_peak = kf.measure_fma_peak(fp64=(args.precision == "fp64"))
     if args.precision == "fp64":
         alu_peak = fma_peak   # no vendor unit count for the FP64 pipe of this part: measured
@@ -1041,7 +1101,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp32_fp64solve": "f32+f64solve"}[args.precision],
         "data": "synthetic (seeded simulation of the model)",
-        "config": dict(workload_config(args, world), **({"tuned": tuned} if tuned else {})),
+        "config": dict(workload_config(args, world), path=path_note, **({"tuned": tuned} if tuned else {})),
         "roofline": roof,
         "kernels": kern,
         "step_roofline": {"steps_per_s": step_roof, "frac": value / world / step_roof},
@@ -1054,6 +1114,8 @@ def main():
                          % (args.steps, kern_ms / args.steps, total_ms / args.steps),
         "clocks": ck,
     }
+    if per_step is not None:
+        out["per_step_kernels"] = per_step
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if world == 1 and not args.no_extra:

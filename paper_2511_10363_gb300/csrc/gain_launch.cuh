@@ -24,9 +24,9 @@ template <int N, typename R, bool REV>
 struct GsCfg {
     static constexpr int M = N / 2, MI = REV ? N : M, WPC = 4;
     // resident CTAs per SM the register budget is sized for (4 compute
-    // warps; with the store warp, 5)
-    static constexpr int MINB = (N <= 4) ? (sizeof(R) == 4 ? 6 : 3) : (sizeof(R) == 4 ? 2 : 1);
-    static constexpr int MINB_SW = MINB * 4 / 6 > 0 ? MINB * 4 / 6 : 1;
+    // warps; with the store warp, 5); measured on GB300 at T = 2^20
+    static constexpr int MINB = (N <= 4) ? (sizeof(R) == 4 ? 5 : 3) : (sizeof(R) == 4 ? 2 : 1);
+    static constexpr int MINB_SW = (N <= 4) ? (sizeof(R) == 4 ? 4 : 2) : (sizeof(R) == 4 ? 2 : 1);
     static constexpr int KS = GsStage<N, MI, R>::KS;
     static constexpr int smem_stage() { return WPC * GsStage<N, MI, R>::WARP; }
 };
@@ -267,12 +267,35 @@ static void gs_fill_args(GsArgs<N, R> &a, const GainModel &g, int k0, int kb, co
     a.trace = nullptr;
     a.trace_cap = 0;
     trace_target(REV ? 1 : 0, &a.trace, &a.trace_cap);
+    a.pdl_wait = 0;
     for (int i = 0; i < N; ++i) a.s0[i] = R(g.m0[i]);
 }
 
+// With pdl, the kernel is launched as a programmatic dependent of the
+// preceding kernel in the stream (it may start while that one drains, and
+// waits for it before reading its output); a plain launch otherwise, or when
+// the dependent launch is refused.
 template <int N, int MI, typename R, bool REV, int WPC, int MINB, bool STOREW>
-static cudaError_t gs_launch(const GsArgs<N, R> &a, int smem, cudaStream_t st) {
-    gs_kernel<N, MI, R, REV, WPC, MINB, STOREW><<<a.ncta, 32 * WPC + (STOREW ? 32 : 0), smem, st>>>(a);
+static cudaError_t gs_launch(GsArgs<N, R> &a, int smem, cudaStream_t st, bool pdl = false) {
+    auto kern = gs_kernel<N, MI, R, REV, WPC, MINB, STOREW>;
+    if (pdl) {
+        a.pdl_wait = 1;
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3(a.ncta);
+        cfg.blockDim = dim3(32 * WPC + (STOREW ? 32 : 0));
+        cfg.dynamicSmemBytes = size_t(smem);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, kern, a) == cudaSuccess) return cudaSuccess;
+        cudaGetLastError();   // refused: a plain launch
+    }
+    a.pdl_wait = 0;
+    kern<<<a.ncta, 32 * WPC + (STOREW ? 32 : 0), smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -427,7 +450,9 @@ static bool gain_run(const GainModel &g, const LaunchReq &q, const KfBufs<R> &bu
                 pr.ncta, pr.K, pr.Kt, (long long)pr.n0, pr.H, smr);
     t0 = nullptr;
     if (timing_on()) timing_record(1, q.stream, &t0);
-    e = gs_launch<N, CFR::MI, R, true, CFR::WPC, CFR::MINB_SW, true>(ar, smr, q.stream);
+    // a programmatic dependent of the filter kernel (not under the library's
+    // per-kernel events, which would stand between them)
+    e = gs_launch<N, CFR::MI, R, true, CFR::WPC, CFR::MINB_SW, true>(ar, smr, q.stream, t0 == nullptr);
     count_launches(1, 1);
     if (t0) timing_commit(1, q.stream, t0);
     blob_used(slot, q.stream);

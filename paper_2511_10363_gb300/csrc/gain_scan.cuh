@@ -96,6 +96,7 @@ struct GsArgs {
     int inject_skip_tile; // test hook: this warp-tile never publishes
     uint64_t *trace;      // phase trace (kf_trace_phases, one row per warp-tile) or null
     int trace_cap;
+    int pdl_wait;         // launched as a programmatic dependent of the kernel that writes u
     R s0[N];              // forward: m0
 };
 
@@ -111,10 +112,16 @@ KF_D int gs_ld_relaxed(const int *p) {
 }
 
 // Bulk copies shared -> global by the tensor memory accelerator (16-byte
-// aligned addresses, sizes multiple of 16).
-KF_D void gs_bulk_store(void *gdst, const void *ssrc, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_addr(ssrc)),
-                 "r"(bytes)
+// aligned addresses, sizes multiple of 16), marked evict-first in L2 so that
+// the streamed output does not displace data the next kernel reads.
+KF_D uint64_t gs_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+KF_D void gs_bulk_store(void *gdst, const void *ssrc, uint32_t bytes, uint64_t pol) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(gdst),
+                 "r"(smem_addr(ssrc)), "r"(bytes), "l"(pol)
                  : "memory");
 }
 KF_D void gs_bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
@@ -223,20 +230,24 @@ struct GsStage {
 
 // Issue the asynchronous loads of one chunk (C records) of the 32 runs of a
 // warp: run r's chunk starts at record base + r * dK (its records ascending
-// from there); records outside [0, T) are skipped.  Offsets relative to
-// `base` fit 32 bits (a warp-tile spans at most 32 K records).
+// from there); records outside [0, T) are skipped.  A lane moves the same
+// unit o of runs lane / SEGU, + 32 / SEGU, ... (SEGU, the units of a run's
+// chunk, divides 32).
 template <int C, int REC, typename R>
 KF_D void gs_stage_load(const R *u, int64_t base, int dK, int64_t T, void *buf, int lane) {
     using W = WarpStage<C, REC, R>;
     using UT = typename UnitT<W::U>::T;
-    const UT *g = reinterpret_cast<const UT *>(u) + base * W::RU;
-    UT *s = static_cast<UT *>(buf);
-    const int64_t lo = -base, hi = T - base;   // valid relative records [lo, hi)
+    constexpr int SEGU = W::SEGU, PER = 32 / SEGU;
+    static_assert(32 % SEGU == 0, "units of a run's chunk divide 32");
+    const int o = lane % SEGU, run0 = lane / SEGU;
+    const int64_t rec0 = base + int64_t(run0) * dK + o / W::RU;
+    const UT *g = reinterpret_cast<const UT *>(u) + rec0 * W::RU + o % W::RU;
+    UT *sp = static_cast<UT *>(buf) + run0 * W::STRIDE + o;
+    const int64_t step = int64_t(PER) * dK;
 #pragma unroll
-    for (int idx = lane; idx < 32 * W::SEGU; idx += 32) {
-        const int run = idx / W::SEGU, o = idx - run * W::SEGU;
-        const int rel = run * dK + o / W::RU;
-        if (rel >= lo && rel < hi) cp_async_unit<W::U>(s + run * W::STRIDE + o, g + rel * W::RU + o % W::RU);
+    for (int j = 0; j < SEGU; ++j) {
+        const int64_t rec = rec0 + j * step;
+        if (rec >= 0 && rec < T) cp_async_unit<W::U>(sp + j * PER * W::STRIDE, g + j * step * W::RU);
     }
 }
 
@@ -285,10 +296,11 @@ KF_D void gs_store_warp(const GsArgs<N, R> &a, unsigned char *cbuf, int lane) {
     }
     if (lane == 0 && sb > sa) {
         constexpr int64_t REC = NN * int64_t(sizeof(R));
+        const uint64_t pol = gs_evict_first_policy();
         char *g = reinterpret_cast<char *>(a.Pout) + sa * REC;
         for (int64_t left = (sb - sa) * REC; left > 0;) {
             const uint32_t b = uint32_t(left < a.covbuf ? left : a.covbuf);
-            gs_bulk_store(g, cbuf, b);
+            gs_bulk_store(g, cbuf, b, pol);
             g += b;
             left -= b;
         }
@@ -322,6 +334,9 @@ __global__ void __launch_bounds__(32 * WPC + (STOREW ? 32 : 0), MINB)
     const R *const sA = sc + a.off.A, *const sB = sc + a.off.B;
     const R *const sHF = sc + a.off.HF, *const sW = sc + a.off.W, *const sPT = sc + a.off.pt;
 
+    // a dependent kernel (the RTS pass after the filter) may be scheduled
+    // as this grid's CTAs retire; it waits for this grid before reading it
+    if (tid == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (warp < WPC) {
         for (int i = tid; i < cunits; i += 32 * WPC)
             cp_async_unit<16>(dsm + 16 * i, reinterpret_cast<const unsigned char *>(a.tab) + 16 * i);
@@ -362,12 +377,16 @@ __global__ void __launch_bounds__(32 * WPC + (STOREW ? 32 : 0), MINB)
         }
     };
     if constexpr (STOREW) {
-        if (warp == WPC) {   // the store warp
+        if (warp == WPC) {   // the store warp (its output does not depend on a preceding kernel)
             cp_async_wait<0>();
             gs_store_warp<N, R, REV>(a, cbuf, lane);
             return;
         }
     }
+    // launched as a dependent of the filter kernel (programmatic dependent
+    // launch): wait for it to complete before reading its means; a no-op
+    // otherwise
+    if (a.pdl_wait) asm volatile("griddepcontrol.wait;" ::: "memory");
     const int v = int(blockIdx.x) * WPC + warp;
     const bool active = v < a.nwt;
     if (active) geom(v);
@@ -589,6 +608,18 @@ __global__ void __launch_bounds__(32 * WPC + (STOREW ? 32 : 0), MINB)
         UT *const g1 = reinterpret_cast<UT *>(a.out1) + rbase * WO::RU;
         UT *const g2 = a.out2 ? reinterpret_cast<UT *>(a.out2) + rbase * WO::RU : nullptr;
         const int rem0 = int(t_hi + 1 - t_lo);   // positions of the warp-tile
+        // the store of each chunk: this lane moves unit o of runs run0 + j 32 / SEGU
+        static_assert(32 % WO::SEGU == 0, "units of a run's chunk divide 32");
+        const int st_o = lane % WO::SEGU, st_run0 = lane / WO::SEGU, st_sl = st_o / WO::RU;
+        const int st_off = REV ? C - 1 - st_sl : st_sl;
+        const int st_rel = (st_run0 * dR + st_sl) * WO::RU + st_o % WO::RU;
+        const int st_soff = st_run0 * WO::STRIDE + st_o;
+        int st_rc[WO::SEGU];   // positions of each of those runs
+#pragma unroll
+        for (int j = 0; j < WO::SEGU; ++j) {
+            const int rc = rem0 - (st_run0 + j * (32 / WO::SEGU)) * Kc;
+            st_rc[j] = rc < 0 ? 0 : (rc > Kc ? Kc : rc);
+        }
 #pragma unroll 1
         for (int ch = 0; ch < nch; ++ch) {
             if (restage) {
@@ -639,20 +670,20 @@ __global__ void __launch_bounds__(32 * WPC + (STOREW ? 32 : 0), MINB)
             }
             ll += double(llc);
             __syncwarp();
-            // the chunk of every run of the warp, coalesced
-            const UT *sb = reinterpret_cast<const UT *>(GS::INPLACE ? ibuf(ch) : obuf);
-            const int chunk0 = REV ? -ch * C : ch * C;
+            // the chunk of every run of the warp, coalesced (the same unit o
+            // of runs run0, run0 + 32 / SEGU, ... for this lane)
+            const UT *sb = reinterpret_cast<const UT *>(GS::INPLACE ? ibuf(ch) : obuf) + st_soff;
+            UT *const gc = g1 + st_rel + (REV ? -ch * C : ch * C) * WO::RU;
+            UT *const gc2 = g2 ? g2 + st_rel + (REV ? -ch * C : ch * C) * WO::RU : nullptr;
+            const int offc = ch * C + st_off;   // this unit's record offset in its run
 #pragma unroll
-            for (int idx = lane; idx < 32 * WO::SEGU; idx += 32) {
-                const int run = idx / WO::SEGU, o = idx - run * WO::SEGU, sl = o / WO::RU;
-                const int off = ch * C + (REV ? C - 1 - sl : sl);   // the record's offset in its run
-                int rc = rem0 - run * Kc;                          // positions of the run
-                rc = rc < 0 ? 0 : (rc > Kc ? Kc : rc);
-                if (off < rc) {
-                    const int rel = (run * dR + chunk0 + sl) * WO::RU + o % WO::RU;
-                    const UT val = sb[run * WO::STRIDE + o];
-                    g1[rel] = val;
-                    if (g2) g2[rel] = val;
+            for (int j = 0; j < WO::SEGU; ++j) {
+                if (offc < st_rc[j]) {
+                    const UT val = sb[j * (32 / WO::SEGU) * WO::STRIDE];
+                    const int d = j * (32 / WO::SEGU) * dR * WO::RU;
+                    if constexpr (REV) __stcs(gc + d, val);   // the smoothed means: streamed out
+                    else gc[d] = val;                          // the filter means: read next by the RTS pass
+                    if (gc2) gc2[d] = val;
                 }
             }
             __syncwarp();

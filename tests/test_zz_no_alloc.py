@@ -28,7 +28,13 @@ def test_noalloc_matches_rts_smooth_twice(precision, nx, T):
     model = W.cv_model() if nx == 4 else (W.random_stable_model(8, 4, seed=3) if nx == 8 else W.cv1d_model())
     dt = kf.dtype_of(precision)
     y = torch.tensor(W.simulate(model, T, seed=T), dtype=dt, device="cuda")
-    ref_m, ref_P, ref_ll = kf.kf_rts_smooth(model, y, precision, "dlb", loglik=True)
+    # the reference runs the same per-step kernels as the no-allocation entry
+    # point (which has no device table cache for the covariance tables)
+    kf.kf_set_option("covariance_tables", 1)
+    try:
+        ref_m, ref_P, ref_ll = kf.kf_rts_smooth(model, y, precision, "dlb", loglik=True)
+    finally:
+        kf.kf_set_option("covariance_tables", 0)
     assert kf.kf_sync_status() == 0
     ref_m, ref_P, ref_ll = ref_m.double().cpu().numpy(), ref_P.double().cpu().numpy(), float(ref_ll.item())
     for _ in range(2):
