@@ -18,7 +18,7 @@ namespace kfs {
 
 // Bytes of the shared buffer of repeated settled covariance records that
 // the bulk copies read (a multiple of every record size, 16 .. 512 bytes).
-constexpr int GS_COVBUF = 2048;
+constexpr int GS_COVBUF = 8192;
 
 template <int N, typename R, bool REV>
 struct GsCfg {
