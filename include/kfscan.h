@@ -94,7 +94,9 @@ typedef enum {
     KF_ERR_BUDGET = 6,   /* serving: job larger than the device budget       */
     KF_ERR_BUSY = 7,     /* serving: queue full / unknown job id             */
     KF_ERR_CAPACITY = 8, /* request larger than a fixed scratch capacity     */
-    KF_ERR_CANCELLED = 9 /* server job cancelled before it started          */
+    KF_ERR_CANCELLED = 9, /* server job cancelled before it started         */
+    KF_ERR_BOUNDS = 10    /* bounds-checked build: an index check failed in a
+                             kernel (the access was skipped)                  */
 } kf_status_t;
 
 typedef struct {
@@ -500,6 +502,13 @@ kf_status_t kf_covariance_tables(const kf_model_t *model, int *k0, int *kb, doub
  * scan (kf_scan_t), threads per CTA, look-back warps and steps per thread,
  * each 0 where the library chooses.  All zero before the first call. */
 kf_status_t kf_last_launch_config(int *scan, int *threads, int *lookback_warps, int *steps_per_thread);
+
+/* 1 in the bounds-checked build of the library (compiled with
+ * KF_BOUNDS_CHECK: the kernels check their indexes into the inputs, outputs,
+ * tables and workspace, record KF_ERR_BOUNDS in the status word on a failed
+ * check and skip that access), else 0.  A debugging build: slower, same
+ * results. */
+int kf_bounds_checked(void);
 kf_status_t kf_tuning_save(const char *path);
 kf_status_t kf_tuning_load(const char *path);
 kf_status_t kf_tuning_clear(void);

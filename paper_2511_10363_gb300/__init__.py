@@ -21,7 +21,8 @@ import numpy as np
 from . import build as _build
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = _build.LIB
+# KFSCAN_LIB selects another build of the library (the bounds-checked one)
+LIB_PATH = os.environ.get("KFSCAN_LIB") or _build.LIB
 
 # enums of kfscan.h
 SCANS = {"auto": 0, "dlb": 1, "decoupled_lookback": 1, "hillis_steele": 2, "hs": 2,
@@ -30,7 +31,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_fp64solve": 2, "mixed": 2}
 OPS = {"filter": 0, "rts": 1, "two_filter": 2, "tf": 2}
 STATUS = {0: "KF_OK", 1: "KF_ERR_ARG", 2: "KF_ERR_NOT_PD", 3: "KF_ERR_CUDA", 4: "KF_ERR_OOM",
           5: "KF_ERR_TIMEOUT", 6: "KF_ERR_BUDGET", 7: "KF_ERR_BUSY", 8: "KF_ERR_CAPACITY",
-          9: "KF_ERR_CANCELLED"}
+          9: "KF_ERR_CANCELLED", 10: "KF_ERR_BOUNDS"}
 OPTIONS = {"wait_timeout_ns": 0, "test_skip_tile": 1, "positions_per_thread": 2, "threads": 3, "general_solve": 4,
            "lookback_warps": 5, "sengupta_n": 6, "filter_kernel": 7,
            "rts_kernel": 8, "covariance_tables": 9}
@@ -97,6 +98,8 @@ def lib():
         DP = ctypes.POINTER(ctypes.c_double)
         L.kf_covariance_tables.argtypes = [MP, IP, IP, DP, DP, DP, DP]
         L.kf_covariance_tables.restype = ctypes.c_int
+        L.kf_bounds_checked.argtypes = []
+        L.kf_bounds_checked.restype = ctypes.c_int
         for f in ("kf_autotune", "kf_tuning_get", "kf_tuning_save", "kf_tuning_load", "kf_tuning_clear",
                   "kf_autotune_batch", "kf_batch_tuning_get", "kf_last_launch_config"):
             getattr(L, f).restype = ctypes.c_int
@@ -668,6 +671,11 @@ def kf_covariance_tables(model):
         return None
     out["k0"], out["kb"] = k0.value, kb.value
     return out
+
+
+def kf_bounds_checked():
+    """True when the loaded library is the bounds-checked build."""
+    return bool(lib().kf_bounds_checked())
 
 
 def kf_last_launch_config():

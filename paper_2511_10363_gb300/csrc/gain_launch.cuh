@@ -268,6 +268,8 @@ static void gs_fill_args(GsArgs<N, R> &a, const GainModel &g, int k0, int kb, co
     a.trace_cap = 0;
     trace_target(REV ? 1 : 0, &a.trace, &a.trace_cap);
     a.pdl_wait = 0;
+    a.tab_len = 0;
+    a.wcap = gwt;
     for (int i = 0; i < N; ++i) a.s0[i] = R(g.m0[i]);
 }
 
@@ -349,14 +351,14 @@ static bool gain_run(const GainModel &g, const LaunchReq &q, const KfBufs<R> &bu
     key = fnv1a(&g.key, sizeof(g.key), key);
     GsOff of, orr;
     memset(&orr, 0, sizeof(orr));
-    size_t rbase = 0;   // the reverse tables' start (values)
+    size_t rbase = 0, tlen = 0;   // the reverse tables' start, the tables' length (values)
     int slot = -1;
     const void *tab = blob_lookup(key, &slot);
     // the offsets of a cached table (a table is built only on a miss)
     static std::mutex omu;
     static uint64_t okey[16];
     static GsOff ooff[16][2];
-    static size_t obase[16];
+    static size_t obase[16], olen[16];
     static int onext = 0;
     bool have = false;
     if (tab) {
@@ -366,6 +368,7 @@ static bool gain_run(const GainModel &g, const LaunchReq &q, const KfBufs<R> &bu
                 of = ooff[i][0];
                 orr = ooff[i][1];
                 rbase = obase[i];
+                tlen = olen[i];
                 have = true;
             }
     }
@@ -377,6 +380,7 @@ static bool gain_run(const GainModel &g, const LaunchReq &q, const KfBufs<R> &bu
             rbase = host.size();
             orr = gs_build<N, R, true>(g, k0, kb, q.T, pr, host);
         }
+        tlen = host.size();
         if (!tab) {
             tab = blob_insert(key, host.data(), host.size() * sizeof(R), q.stream, &slot);
             if (!tab) return false;
@@ -386,6 +390,7 @@ static bool gain_run(const GainModel &g, const LaunchReq &q, const KfBufs<R> &bu
         ooff[onext][0] = of;
         ooff[onext][1] = orr;
         obase[onext] = rbase;
+        olen[onext] = tlen;
         onext = (onext + 1) % 16;
     }
     if (int(sizeof(R)) * of.nconst > cbytes || (rts && int(sizeof(R)) * orr.nconst > cbytes)) return false;
@@ -403,6 +408,7 @@ static bool gain_run(const GainModel &g, const LaunchReq &q, const KfBufs<R> &bu
     // forward: filter means (the RTS pass's input record, and the user's copy)
     GsArgs<N, R> af;
     gs_fill_args<N, R, false>(af, g, k0, kb, q, pf, dtab, of, gw, cap);
+    af.tab_len = int64_t(rts ? rbase : tlen);
     af.u = buf.y;
     af.out1 = xrec;
     af.out2 = (rts && buf.mf_user) ? buf.mf_user : nullptr;
@@ -438,6 +444,7 @@ static bool gain_run(const GainModel &g, const LaunchReq &q, const KfBufs<R> &bu
     // reverse: smoothed means and covariances
     GsArgs<N, R> ar;
     gs_fill_args<N, R, true>(ar, g, k0, kb, q, pr, dtab + rbase, orr, gw, cap);
+    ar.tab_len = int64_t(tlen - rbase);
     ar.u = xrec;
     ar.out1 = buf.ms;
     ar.out2 = nullptr;

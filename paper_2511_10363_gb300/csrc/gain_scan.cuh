@@ -53,6 +53,9 @@
 
 namespace kfs {
 
+// index checks of the bounds-checked build, against this kernel's status word
+#define GS_IN(cond) KF_IN(cond, a.status)
+
 // Offsets (in values of type R) into the device tables of one direction.
 // The constant block [0, nconst) is copied to shared memory by every CTA.
 struct GsOff {
@@ -97,6 +100,8 @@ struct GsArgs {
     uint64_t *trace;      // phase trace (kf_trace_phases, one row per warp-tile) or null
     int trace_cap;
     int pdl_wait;         // launched as a programmatic dependent of the kernel that writes u
+    int64_t tab_len;      // values of the table from tab on (index checks of a bounds-checked build)
+    int64_t wcap;         // warp-tiles the words and ll_part hold
     R s0[N];              // forward: m0
 };
 
@@ -270,7 +275,9 @@ KF_D void gs_store_cov(const GsArgs<N, R> &a, int64_t r0, int64_t r1, int lane) 
     const int part = lane % UPR;
     for (int64_t i = lane; i < (r1 - r0) * UPR; i += 32) {
         const int64_t r = r0 + i / UPR;
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(gs_cov_src<N, R, REV>(a, r)) + part);
+        const R *src = gs_cov_src<N, R, REV>(a, r);
+        if (!GS_IN(r >= 0 && r < a.T && src >= a.tab && src + N * N <= a.tab + a.tab_len)) continue;
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(src) + part);
         __stcs(g + r0 * UPR + i, v);
     }
 }
@@ -294,7 +301,7 @@ KF_D void gs_store_warp(const GsArgs<N, R> &a, unsigned char *cbuf, int lane) {
         gs_fence_async_shared();
         __syncwarp();
     }
-    if (lane == 0 && sb > sa) {
+    if (lane == 0 && sb > sa && GS_IN(sa >= 0 && sb <= a.T)) {
         constexpr int64_t REC = NN * int64_t(sizeof(R));
         const uint64_t pol = gs_evict_first_policy();
         char *g = reinterpret_cast<char *>(a.Pout) + sa * REC;
@@ -337,7 +344,7 @@ __global__ void __launch_bounds__(32 * WPC + (STOREW ? 32 : 0), MINB)
     // a dependent kernel (the RTS pass after the filter) may be scheduled
     // as this grid's CTAs retire; it waits for this grid before reading it
     if (tid == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    if (warp < WPC) {
+    if (warp < WPC && GS_IN(int64_t(cunits) * 16 <= a.tab_len * int64_t(sizeof(R)))) {
         for (int i = tid; i < cunits; i += 32 * WPC)
             cp_async_unit<16>(dsm + 16 * i, reinterpret_cast<const unsigned char *>(a.tab) + 16 * i);
     }
@@ -419,7 +426,7 @@ __global__ void __launch_bounds__(32 * WPC + (STOREW ? 32 : 0), MINB)
     // time when it lies in 1..k0, else the settled ones
     auto coef = [&](int64_t j, const R *&A, const R *&B, const R *&Wk) {
         const int64_t tk = REV ? a.T - j : j;
-        if (tk <= a.k0) {
+        if (tk <= a.k0 && GS_IN(tk >= 1 && a.off.tB + tk * N * MI <= a.tab_len && a.off.tA + tk * NN <= a.tab_len)) {
             A = a.tab + a.off.tA + (tk - 1) * NN;
             B = a.tab + a.off.tB + (tk - 1) * N * MI;
             Wk = REV ? sW : a.tab + a.off.tW + (tk - 1) * M * M;
@@ -474,6 +481,7 @@ __global__ void __launch_bounds__(32 * WPC + (STOREW ? 32 : 0), MINB)
             if (gen) {
                 R Wm[NN];
                 const R *g = a.tab + a.off.gwin + (i * 32 + lane) * NN;
+                if (!GS_IN(a.off.gwin + (i * 32 + lane + 1) * int64_t(NN) <= a.tab_len)) g = a.tab;
 #pragma unroll
                 for (int k = 0; k < NN; ++k) Wm[k] = __ldg(g + k);
                 gs_mva<N, R>(Wm, x, phi);
@@ -495,6 +503,7 @@ __global__ void __launch_bounds__(32 * WPC + (STOREW ? 32 : 0), MINB)
     // known), a bulk warp-tile its aggregate; 4. the carry c
     R c[N];
     uint64_t *const myw = a.words + int64_t(v) * a.wstride;
+    if (!GS_IN(v < a.wcap)) return;
     if (v == 0) {
         if constexpr (!REV) {
 #pragma unroll
@@ -530,7 +539,7 @@ __global__ void __launch_bounds__(32 * WPC + (STOREW ? 32 : 0), MINB)
         const uint64_t t0 = gs_ns();
         const unsigned all = n >= 32 ? 0xffffffffu : (1u << n) - 1u;
         for (;;) {
-            if (lane < n && !hi) {
+            if (lane < n && !hi && GS_IN(int64_t(v) - 1 - lane >= 0)) {
                 hi = gs_get<N, R>(qw + NWD, vi);
                 if (!hi && !ha) ha = gs_get<N, R>(qw, va);
             }
@@ -678,9 +687,12 @@ __global__ void __launch_bounds__(32 * WPC + (STOREW ? 32 : 0), MINB)
             const int offc = ch * C + st_off;   // this unit's record offset in its run
 #pragma unroll
             for (int j = 0; j < WO::SEGU; ++j) {
-                if (offc < st_rc[j]) {
+                const int d = j * (32 / WO::SEGU) * dR * WO::RU;
+                // (the record stored: rbase + (run0 + j 32 / SEGU) dR + slot +- ch C)
+                if (offc < st_rc[j] &&
+                    GS_IN(rbase + (st_run0 + j * (32 / WO::SEGU)) * dR + st_sl + (REV ? -ch * C : ch * C) >= 0 &&
+                          rbase + (st_run0 + j * (32 / WO::SEGU)) * dR + st_sl + (REV ? -ch * C : ch * C) < a.T)) {
                     const UT val = sb[j * (32 / WO::SEGU) * WO::STRIDE];
-                    const int d = j * (32 / WO::SEGU) * dR * WO::RU;
                     if constexpr (REV) __stcs(gc + d, val);   // the smoothed means: streamed out
                     else gc[d] = val;                          // the filter means: read next by the RTS pass
                     if (gc2) gc2[d] = val;
@@ -701,7 +713,7 @@ __global__ void __launch_bounds__(32 * WPC + (STOREW ? 32 : 0), MINB)
 #pragma unroll
             for (int s2 = 16; s2 > 0; s2 >>= 1) ll += __shfl_down_sync(0xffffffffu, ll, s2);
             int last = 0;
-            if (lane == 0) {
+            if (lane == 0 && GS_IN(v < a.wcap)) {
                 a.ll_part[v] = ll;
                 __threadfence();
                 last = atomicAdd(a.counters + 1, 1) == a.nwt - 1;

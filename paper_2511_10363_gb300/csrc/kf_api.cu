@@ -971,6 +971,14 @@ using namespace kfs;
 
 extern "C" {
 
+int kf_bounds_checked(void) {
+#ifdef KF_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 const char *kf_status_string(kf_status_t s) {
     switch (s) {
         case KF_OK: return "ok";
@@ -983,6 +991,7 @@ const char *kf_status_string(kf_status_t s) {
         case KF_ERR_BUSY: return "queue full or unknown job";
         case KF_ERR_CAPACITY: return "request exceeds a fixed scratch capacity";
         case KF_ERR_CANCELLED: return "job cancelled before it started";
+        case KF_ERR_BOUNDS: return "an index check failed in a kernel (bounds-checked build)";
     }
     return "unknown status";
 }

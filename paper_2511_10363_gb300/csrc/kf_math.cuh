@@ -25,6 +25,20 @@
 
 namespace kfs {
 
+// Index checks of the bounds-checked build (compiled with KF_BOUNDS_CHECK):
+// a failed check records KF_ERR_BOUNDS (10) in the status word, unless it
+// already holds an error, and the access it guards is skipped.  In the
+// normal build every check is the constant true.
+#if defined(KF_BOUNDS_CHECK) && defined(__CUDACC__)
+KF_D bool kf_in(bool ok, int *status) {
+    if (!ok) atomicCAS(status, 0, 10);
+    return ok;
+}
+#define KF_IN(cond, status) ::kfs::kf_in((cond), (status))
+#else
+#define KF_IN(cond, status) true
+#endif
+
 constexpr int MAXNY = 8;
 
 // packed upper-triangular index, row-major over i <= j

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(THREADS, MINB) rts_kernel(const __grid_constan
     if (trace) trace[0] = rs_ns();
     const int64_t T = a.T;
     const int64_t r0 = (int64_t(tile) * THREADS + tid) * a.K;   // this thread's first scan position
-    const int64_t r1 = r0 + a.K < T ? r0 + a.K : T;             // one past its last
+    const int64_t r1 = KF_IN(r0 >= 0, a.status) ? (r0 + a.K < T ? r0 + a.K : T) : r0;   // one past its last
     const int64_t start0 = (int64_t(tile) * THREADS + warp * 32) * a.K;   // lane 0's first position
 
     // ---- fold: the aggregate of this thread's K elements (scan order is
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(THREADS, MINB) rts_kernel(const __grid_constan
             int qloc = -1;
             for (int q0 = tile - 1; q0 >= 0 && ok; q0 -= 32) {
                 const int q = q0 - lane;
-                int f = q >= 0 ? rs_ld_relaxed(a.flags + q) : 1;
+                int f = q >= 0 && KF_IN(q < a.ntiles, a.status) ? rs_ld_relaxed(a.flags + q) : 1;
                 unsigned ns = 32;
                 const uint64_t t0 = rs_ns();
                 while (!__all_sync(0xffffffffu, f != 0)) {

@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
     // published at once (flag 2), so later look-backs stop there.
     constexpr int ESP = padded_size<Elem, R>();
     const bool zt = tile > 0 && P::zero_transition(tagg);
-    if (tile > 0 && tid == 0) {
+    if (tile > 0 && tid == 0 && KF_IN(tile < ctl.ntiles, ctl.status)) {
         if (zt) {
             Carry inc;
             P::carry_of(tagg, inc);
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
             int qloc = -1;
             for (int q0 = tile - 1; q0 >= 0 && ok; q0 -= 32) {
                 const int q = q0 - lane;
-                int f = q >= 0 ? ld_relaxed(ctl.flags + q) : 1;
+                int f = q >= 0 && KF_IN(q < ctl.ntiles, ctl.status) ? ld_relaxed(ctl.flags + q) : 1;
                 unsigned ns = 32;
                 const uint64_t t0 = global_ns();
                 while (!__all_sync(0xffffffffu, f != 0)) {
@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
         if (lane == 0) {
 #pragma unroll
             for (int i = 0; i < CS; ++i) s_carry[i] = tc.v[i];
-            if (!zt) {   // (already published when the transition is zero)
+            if (!zt && KF_IN(tile < ctl.ntiles, ctl.status)) {   // (already published when the transition is zero)
                 R *dst = static_cast<R *>(ctl.incl) + int64_t(tile) * CS;
 #pragma unroll
                 for (int i = 0; i < CS; ++i) dst[i] = inc.v[i];
@@ -621,6 +621,7 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
                                 : (P::O2 && oarr[1]) ? oarr[1] + g * P::O2 : nullptr;
                 R *o3 = obuf[2] ? stage_rec<C, (P::O3 ? P::O3 : 1), R>(obuf[2], lane, slot)
                                 : (P::O3 && oarr[2]) ? oarr[2] + g * P::O3 : nullptr;
+                if (!KF_IN(g >= 0 && g < total, ctl.status)) continue;
                 const R l = P::step_at(args, p, cur, c, in, o1, o2, o3);
                 llc += l;
                 if (ctl.ll_step) ctl.ll_step[g] = double(l);
@@ -649,7 +650,7 @@ __global__ void __launch_bounds__(THREADS, (dlb_min_blocks<P, THREADS>())) dlb_s
         if (tid == 0) {
             double t = 0.0;
             for (int w = 0; w < NW; ++w) t += s_ll[w];
-            ctl.ll_part[tile] = t;
+            if (KF_IN(tile < ctl.ntiles, ctl.status)) ctl.ll_part[tile] = t;
             __threadfence();
             s_last = (atomicAdd(ctl.counters + 1, 1) == ctl.ntiles - 1);
         }

@@ -281,6 +281,7 @@ KF_D void ti_emit(const TiArgs<N, R> &a, int64_t g, const R *b, const R *C, R *s
         for (int i = N + S; i < FR; ++i) rec[i] = 0;
         store_rec<FR>(srec, rec);
     }
+    if (!KF_IN(g >= 0 && g < a.T, a.status)) return;
     if (a.mf) store_rec<N>(a.mf + g * N, b);
     if (a.Pf) {
         R full[N * N];
@@ -515,7 +516,7 @@ __global__ void __launch_bounds__(THREADS, MINB) ti_filter_kernel(const __grid_c
             bool ok = true;
             for (int q0 = xz ? tile - 1 : 0; q0 < tile && ok; q0 += 32) {
                 const int q = q0 + lane;
-                bool seen = q >= tile || ti_ld_relaxed(a.flags + q) != 0;
+                bool seen = q >= tile || !KF_IN(q >= 0, a.status) || ti_ld_relaxed(a.flags + q) != 0;
                 unsigned ns = 32;
                 const uint64_t t0 = ti_ns();
                 while (!__all_sync(0xffffffffu, seen)) {
