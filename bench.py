@@ -146,15 +146,16 @@ def job_rate(world, steps, T, max_ms):
 
 # ------------------------------------------------------------------ DRAM traffic
 
-def kernel_source_hash():
-    """sha256 over the sources the time-invariant scan kernels compile from --
-    the per-size launch units (kf_n<N>_<precision>*.cu) and every header they
+def kernel_source_hash(units=r"kf_n\d+_\w+\.cu$"):
+    """sha256 over the sources a path's scan kernels compile from -- its
+    per-size launch units (kf_n<N>_<precision>*.cu for the per-step kernels,
+    gs_n<N>_<precision>.cu for the covariance tables) and every header they
     include -- so that a recorded ncu traffic figure is used only for the
     kernels it was measured on."""
     import hashlib
     import re
     d = os.path.join(ROOT, "paper_2511_10363_gb300", "csrc")
-    todo = [f for f in sorted(os.listdir(d)) if re.match(r"kf_n\d+_\w+\.cu$", f)]
+    todo = [f for f in sorted(os.listdir(d)) if re.match(units, f)]
     seen = set()
     while todo:
         f = todo.pop()
@@ -170,14 +171,14 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, precision, T, cfg):
+def recorded_traffic(kernel, precision, T, cfg, units=r"kf_n\d+_\w+\.cu$"):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
     recorded under profiles/ for this kernel, workload and launch
     configuration; None when absent or measured on other kernel sources."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    want = kernel_source_hash()
+    want = kernel_source_hash(units)
     for line in open(path):
         f = line.split()
         if len(f) == 6 and not line.startswith("#"):
@@ -1085,7 +1086,10 @@ def main():
     d = kern[dom]
     cfgname = "threads%d_lbw%d_k%d" % ((tuned["threads"], tuned["lookback_warps"], tuned["steps_per_thread"])
                                       if tuned else (args.threads, args.lbw, args.k))
-    traffic = recorded_traffic(dom, args.precision, T, cfgname)
+    if gain_path:
+        traffic = recorded_traffic(dom, args.precision, T, "covariance_tables", r"gs_n\d+_\w+\.cu$")
+    else:
+        traffic = recorded_traffic(dom, args.precision, T, cfgname)
     if d["bound"] == "alu":
         roof = {"kernel": dom, "bound": "alu", "achieved": d["tflops"], "peak": alu_peak / 1e12, "unit": "TFLOP/s",
                 "frac": d["frac"], "traffic": traffic,
