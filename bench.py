@@ -532,18 +532,17 @@ def workload_mixed(args):
                       "results": res}))
 
 
-def workload_tv(args):
+def tv_results(T, precs=("fp32", "fp64")):
     """Time-varying tracking model (per-step F, Q, u, H, R, d of Sec. III-A;
-    nx = 4, ny = 2), T = --T (default 2^20): kf_tv_rts_smooth with the
-    log-likelihood, FP32 and FP64, beside kf_rts_smooth on a time-invariant
-    model of the same size.  Per-kernel times come from the library's CUDA
-    events; the roofline is HBM with the algorithmic bytes of a smoothed step
-    (inputs of the filter pass, F, Q, u again in the RTS pass, the filter
-    record written and read back, the smoothed mean and covariance).  The
-    inputs exceed L2 at this T, so no flush is done between runs."""
+    nx = 4, ny = 2), T steps: kf_tv_rts_smooth with the log-likelihood in
+    each precision, beside kf_rts_smooth on a time-invariant model of the
+    same size.  Per-kernel times come from the library's CUDA events; the
+    roofline is HBM with the algorithmic bytes of a smoothed step (inputs of
+    the filter pass, F, Q, u again in the RTS pass, the filter record written
+    and read back, the smoothed mean and covariance).  The inputs exceed L2
+    at T = 2^20, so no flush is done between runs."""
     import torch
     import paper_2511_10363_gb300 as kf
-    T = args.T
     nx, ny = 4, 2
     model = W.tv_model(nx, T, seed=2)
     y64 = W.simulate_tv(model, seed=3)
@@ -554,7 +553,7 @@ def workload_tv(args):
     rec_vals = nx + nx * (nx + 1) // 2
     vals = (ny + 2 * nx * nx + nx + ny * nx + ny * ny + ny) + (2 * nx * nx + nx) + 2 * rec_vals + (nx + nx * nx)
     res = {}
-    for prec in ("fp32", "fp64"):
+    for prec in precs:
         dt = kf.dtype_of(prec)
         w = 8 if prec == "fp64" else 4
         tm = kf.TvModel(model, prec, "cuda")
@@ -588,11 +587,16 @@ def workload_tv(args):
                                   "unit": "GB/s", "frac": gbs / hbm,
                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
         del ws
-    print(json.dumps({"workload": "tv", "metric": "smoothed steps/s", "unit": "smoothed steps/s",
-                      "model": "time-varying 2D constant-velocity tracking nx=4 ny=2 with inputs u, d", "T": T,
-                      "op": "rts (filter + smoother) with log-likelihood, decoupled look-back",
-                      "timing": "median of 10 after 2 dropped runs (CUDA events); inputs larger than L2",
-                      "results": res}))
+    return {"metric": "smoothed steps/s", "unit": "smoothed steps/s",
+            "model": "time-varying 2D constant-velocity tracking nx=4 ny=2 with inputs u, d", "T": T,
+            "op": "rts (filter + smoother) with log-likelihood, decoupled look-back",
+            "timing": "median of 10 after 2 dropped runs (CUDA events); inputs larger than L2",
+            "results": res}
+
+
+def workload_tv(args):
+    """The time-varying model at T = --T (default 2^20), FP32 and FP64."""
+    print(json.dumps(dict(workload="tv", **tv_results(args.T))))
 
 
 def cpu_baseline_jobs(jobs, what, seconds=10.0):
@@ -1125,9 +1129,12 @@ def main():
     if world == 1 and not args.no_extra:
         out["accuracy"] = accuracy_vs_oracle(args, model, y_host, ms, Ps, ll if want_ll else None)
         # the metric's second half: batched and served forms against plain
-        # one-call-per-request launches on the same GPU (SURVEY configs 4, 5)
+        # one-call-per-request launches on the same GPU (the batch and
+        # serving configurations)
         out["batch"] = run_batch(precs=("fp32",), with_cpu=not args.no_cpu_baseline)
         out["serving"] = run_serving(2000.0, 10.0, with_cpu=not args.no_cpu_baseline)
+        # the time-varying model of the paper's experiments at the same T (FP32)
+        out["tv"] = tv_results(T, ("fp32",))
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()

@@ -392,6 +392,16 @@ kf_status_t kf_stream_status(void *stream);
  *                               (the lengths of the two transients, a few
  *                               hundred steps for a well-damped model).
  *                               1: the per-step kernels above.
+ *   KF_OPT_CALL_GRAPHS          1 (default): a covariance-table call whose
+ *                               launches repeat an earlier call's exactly
+ *                               (same buffers, length, model, options and
+ *                               device) is replayed from a CUDA graph of its
+ *                               memset and both kernels, captured on a
+ *                               private stream at the second such call (8
+ *                               graphs per state size and precision, least
+ *                               recently used replaced); calls on a stream
+ *                               under capture, with kernel timing or phase
+ *                               tracing launch directly.  0: always direct.
  * Returns KF_ERR_ARG for an unknown option or a value out of range. */
 typedef enum {
     KF_OPT_WAIT_TIMEOUT_NS = 0,
@@ -403,7 +413,8 @@ typedef enum {
     KF_OPT_SENGUPTA_N = 6,
     KF_OPT_FILTER_KERNEL = 7,
     KF_OPT_RTS_KERNEL = 8,
-    KF_OPT_COVARIANCE_TABLES = 9
+    KF_OPT_COVARIANCE_TABLES = 9,
+    KF_OPT_CALL_GRAPHS = 10
 } kf_option_t;
 kf_status_t kf_set_option(kf_option_t opt, int64_t value);
 int64_t kf_get_option(kf_option_t opt); /* -1 for an unknown option */
@@ -509,6 +520,10 @@ kf_status_t kf_last_launch_config(int *scan, int *threads, int *lookback_warps, 
  * check and skip that access), else 0.  A debugging build: slower, same
  * results. */
 int kf_bounds_checked(void);
+
+/* Call graphs (KF_OPT_CALL_GRAPHS) captured and replayed since the library
+ * was loaded, over all threads and devices (either pointer may be NULL). */
+kf_status_t kf_call_graph_stats(int64_t *captured, int64_t *replayed);
 kf_status_t kf_tuning_save(const char *path);
 kf_status_t kf_tuning_load(const char *path);
 kf_status_t kf_tuning_clear(void);

@@ -34,7 +34,7 @@ STATUS = {0: "KF_OK", 1: "KF_ERR_ARG", 2: "KF_ERR_NOT_PD", 3: "KF_ERR_CUDA", 4: 
           9: "KF_ERR_CANCELLED", 10: "KF_ERR_BOUNDS"}
 OPTIONS = {"wait_timeout_ns": 0, "test_skip_tile": 1, "positions_per_thread": 2, "threads": 3, "general_solve": 4,
            "lookback_warps": 5, "sengupta_n": 6, "filter_kernel": 7,
-           "rts_kernel": 8, "covariance_tables": 9}
+           "rts_kernel": 8, "covariance_tables": 9, "call_graphs": 10}
 
 _lib = None
 
@@ -98,6 +98,8 @@ def lib():
         DP = ctypes.POINTER(ctypes.c_double)
         L.kf_covariance_tables.argtypes = [MP, IP, IP, DP, DP, DP, DP]
         L.kf_covariance_tables.restype = ctypes.c_int
+        L.kf_call_graph_stats.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.kf_call_graph_stats.restype = ctypes.c_int
         L.kf_bounds_checked.argtypes = []
         L.kf_bounds_checked.restype = ctypes.c_int
         for f in ("kf_autotune", "kf_tuning_get", "kf_tuning_save", "kf_tuning_load", "kf_tuning_clear",
@@ -671,6 +673,13 @@ def kf_covariance_tables(model):
         return None
     out["k0"], out["kb"] = k0.value, kb.value
     return out
+
+
+def kf_call_graph_stats():
+    """Call graphs captured and replayed since the library was loaded."""
+    c, r = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().kf_call_graph_stats(ctypes.byref(c), ctypes.byref(r)), "kf_call_graph_stats")
+    return {"captured": c.value, "replayed": r.value}
 
 
 def kf_bounds_checked():

@@ -301,6 +301,116 @@ static cudaError_t gs_launch(GsArgs<N, R> &a, int smem, cudaStream_t st, bool pd
     return cudaGetLastError();
 }
 
+// ---- call graphs
+// A call whose launches repeat an earlier call's byte for byte (the same
+// buffers, length, model tables, options and device: the key is the
+// launches' argument bytes) replays a CUDA graph of its memset and both
+// kernels, with the programmatic dependency between them, as one launch.
+// The graph is captured on a private stream at the second such call (the
+// first only records the key), and launched on the caller's stream; a
+// capture that fails is not tried again for that key.  Calls on a stream
+// that is itself under capture launch directly.
+struct GsGraphEntry {
+    std::vector<unsigned char> key;
+    uint64_t h = 0, stamp = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;   // after the last launch of exec (waited on before it is destroyed)
+    bool failed = false;
+};
+
+template <int N, typename R>
+struct GsGraphs {
+    std::mutex mu;
+    GsGraphEntry e[8];
+    uint64_t clock = 0;
+    cudaStream_t cap[64] = {};
+};
+
+template <int N, typename R>
+static GsGraphs<N, R> &gs_graphs() {
+    static GsGraphs<N, R> g;
+    return g;
+}
+
+static inline void gs_graph_release(GsGraphEntry &x) {
+    if (x.exec) {
+        if (x.done) cudaEventSynchronize(x.done);
+        cudaGraphExecDestroy(x.exec);
+        x.exec = nullptr;
+    }
+}
+
+// The graph of this key, captured now if the key was seen before; false
+// when the call is to launch directly (first sighting, failed capture,
+// stream under capture).
+template <int N, typename R, class Enq>
+static bool gs_graph_get(int dev, cudaStream_t st, const std::vector<unsigned char> &key, Enq &enqueue,
+                         cudaGraphExec_t *exec, cudaEvent_t *done) {
+    if (dev < 0 || dev >= 64) return false;
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cst) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cst != cudaStreamCaptureStatusNone) return false;
+    GsGraphs<N, R> &G = gs_graphs<N, R>();
+    std::lock_guard<std::mutex> lk(G.mu);
+    const uint64_t h = fnv1a(key.data(), key.size(), 0x9e37u);
+    GsGraphEntry *x = nullptr;
+    for (auto &c : G.e)
+        if (c.h == h && c.key == key) x = &c;
+    if (!x) {   // first sighting: remember the key (replacing the least recently used)
+        x = &G.e[0];
+        for (auto &c : G.e)
+            if (c.stamp < x->stamp) x = &c;
+        gs_graph_release(*x);
+        x->key = key;
+        x->h = h;
+        x->failed = false;
+        x->stamp = ++G.clock;
+        return false;
+    }
+    x->stamp = ++G.clock;
+    if (x->failed) return false;
+    if (!x->exec) {
+        bool ok = false;
+        cudaStream_t cs = G.cap[dev];
+        if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) G.cap[dev] = cs;
+        if (cs && (x->done || cudaEventCreateWithFlags(&x->done, cudaEventDisableTiming) == cudaSuccess) &&
+            cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const cudaError_t eq = enqueue(cs, false);
+            cudaGraph_t gr = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(cs, &gr);
+            if (eq == cudaSuccess && ec == cudaSuccess && gr && cudaGraphInstantiate(&x->exec, gr, 0) == cudaSuccess) {
+                ok = true;
+                count_graph(0);
+            }
+            if (gr) cudaGraphDestroy(gr);
+        }
+        if (!ok) {
+            cudaGetLastError();
+            x->exec = nullptr;
+            x->failed = true;
+            return false;
+        }
+    }
+    *exec = x->exec;
+    *done = x->done;
+    return true;
+}
+
+// A graph that did not launch: launch this key directly from now on.
+template <int N, typename R>
+static void gs_graph_fail(const std::vector<unsigned char> &key) {
+    GsGraphs<N, R> &G = gs_graphs<N, R>();
+    std::lock_guard<std::mutex> lk(G.mu);
+    for (auto &c : G.e)
+        if (c.key == key) {
+            gs_graph_release(c);
+            c.failed = true;
+        }
+}
+
 static inline bool gs_al16(const void *p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 // Runs the filter (and, for the RTS smoother, the RTS pass) on the
@@ -399,14 +509,11 @@ static bool gain_run(const GainModel &g, const LaunchReq &q, const KfBufs<R> &bu
     // counters and published words of both directions: one memset
     char *gw = ws + L.gw;
     const int ntmax = rts && pr.nwt > pf.nwt ? pr.nwt : pf.nwt;
-    cudaError_t e = cudaMemsetAsync(gw, 0, 256 + size_t(ntmax) * GL::STRIDE * 8, q.stream);
-    if (e != cudaSuccess) {
-        *err = e;
-        return true;
-    }
+    const size_t gw_bytes = 256 + size_t(ntmax) * GL::STRIDE * 8;
 
     // forward: filter means (the RTS pass's input record, and the user's copy)
     GsArgs<N, R> af;
+    memset(&af, 0, sizeof(af));   // (padding too: the arguments' bytes key the call graphs)
     gs_fill_args<N, R, false>(af, g, k0, kb, q, pf, dtab, of, gw, cap);
     af.tab_len = int64_t(rts ? rbase : tlen);
     af.u = buf.y;
@@ -429,39 +536,82 @@ static bool gain_run(const GainModel &g, const LaunchReq &q, const KfBufs<R> &bu
         fprintf(stderr,
                 "[kfscan] gain filter: T=%lld k0=%d kb=%d warp-tiles=%d ctas=%d K=%d Kt=%d n0=%lld H=%d smem=%d\n",
                 (long long)q.T, k0, kb, pf.nwt, pf.ncta, pf.K, pf.Kt, (long long)pf.n0, pf.H, smf);
-    cudaEvent_t t0 = nullptr;
-    if (timing_on()) timing_record(0, q.stream, &t0);
-    e = pf_out ? gs_launch<N, CFF::MI, R, false, CFF::WPC, CFF::MINB_SW, true>(af, smf, q.stream)
-               : gs_launch<N, CFF::MI, R, false, CFF::WPC, CFF::MINB, false>(af, smf, q.stream);
-    count_launches(0, 1);
-    if (t0) timing_commit(0, q.stream, t0);
-    if (e != cudaSuccess || !rts) {
-        blob_used(slot, q.stream);
-        *err = e;
-        return true;
-    }
 
     // reverse: smoothed means and covariances
     GsArgs<N, R> ar;
-    gs_fill_args<N, R, true>(ar, g, k0, kb, q, pr, dtab + rbase, orr, gw, cap);
-    ar.tab_len = int64_t(tlen - rbase);
-    ar.u = xrec;
-    ar.out1 = buf.ms;
-    ar.out2 = nullptr;
-    ar.Pout = buf.Ps;
-    ar.covbuf = GS_COVBUF;
-    ar.cov_slice = (q.T + pr.ncta - 1) / pr.ncta;
-    const int smr = CFR::smem_stage() + (int(sizeof(R)) * orr.nconst + 15) / 16 * 16 + GS_COVBUF;
-    if (debug_on())
-        fprintf(stderr, "[kfscan] gain rts: warp-tiles=%d ctas=%d K=%d Kt=%d n0=%lld H=%d smem=%d\n", pr.nwt,
-                pr.ncta, pr.K, pr.Kt, (long long)pr.n0, pr.H, smr);
-    t0 = nullptr;
-    if (timing_on()) timing_record(1, q.stream, &t0);
-    // a programmatic dependent of the filter kernel (not under the library's
-    // per-kernel events, which would stand between them)
-    e = gs_launch<N, CFR::MI, R, true, CFR::WPC, CFR::MINB_SW, true>(ar, smr, q.stream, t0 == nullptr);
-    count_launches(1, 1);
-    if (t0) timing_commit(1, q.stream, t0);
+    memset(&ar, 0, sizeof(ar));
+    int smr = 0;
+    if (rts) {
+        gs_fill_args<N, R, true>(ar, g, k0, kb, q, pr, dtab + rbase, orr, gw, cap);
+        ar.tab_len = int64_t(tlen - rbase);
+        ar.u = xrec;
+        ar.out1 = buf.ms;
+        ar.out2 = nullptr;
+        ar.Pout = buf.Ps;
+        ar.covbuf = GS_COVBUF;
+        ar.cov_slice = (q.T + pr.ncta - 1) / pr.ncta;
+        smr = CFR::smem_stage() + (int(sizeof(R)) * orr.nconst + 15) / 16 * 16 + GS_COVBUF;
+        if (debug_on())
+            fprintf(stderr, "[kfscan] gain rts: warp-tiles=%d ctas=%d K=%d Kt=%d n0=%lld H=%d smem=%d\n", pr.nwt,
+                    pr.ncta, pr.K, pr.Kt, (long long)pr.n0, pr.H, smr);
+    }
+
+    // the memset and the launches of this call on stream st; with timing,
+    // library events around each kernel (the reverse launch is then not a
+    // programmatic dependent: the events stand between the kernels)
+    auto enqueue = [&](cudaStream_t st, bool timing) -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(gw, 0, gw_bytes, st);
+        if (e != cudaSuccess) return e;
+        GsArgs<N, R> a1 = af;
+        cudaEvent_t t0 = nullptr;
+        if (timing) timing_record(0, st, &t0);
+        e = pf_out ? gs_launch<N, CFF::MI, R, false, CFF::WPC, CFF::MINB_SW, true>(a1, smf, st)
+                   : gs_launch<N, CFF::MI, R, false, CFF::WPC, CFF::MINB, false>(a1, smf, st);
+        if (t0) timing_commit(0, st, t0);
+        if (e != cudaSuccess || !rts) return e;
+        GsArgs<N, R> a2 = ar;
+        t0 = nullptr;
+        if (timing) timing_record(1, st, &t0);
+        e = gs_launch<N, CFR::MI, R, true, CFR::WPC, CFR::MINB_SW, true>(a2, smr, st, t0 == nullptr);
+        if (t0) timing_commit(1, st, t0);
+        return e;
+    };
+
+    // a repeated call: replay its graph
+    if (q.call_graphs && !timing_on() && !af.trace && !ar.trace && q.inject_skip_tile < 0) {
+        std::vector<unsigned char> key;
+        auto put = [&key](const void *p, size_t n) {
+            key.insert(key.end(), static_cast<const unsigned char *>(p), static_cast<const unsigned char *>(p) + n);
+        };
+        const int flags = (rts ? 1 : 0) | (pf_out ? 2 : 0);
+        put(&dev, sizeof(dev));
+        put(&flags, sizeof(flags));
+        put(&gw, sizeof(gw));
+        put(&gw_bytes, sizeof(gw_bytes));
+        put(&smf, sizeof(smf));
+        put(&smr, sizeof(smr));
+        put(&af, sizeof(af));
+        put(&ar, sizeof(ar));
+        cudaGraphExec_t exec = nullptr;
+        cudaEvent_t done = nullptr;
+        if (gs_graph_get<N, R>(dev, q.stream, key, enqueue, &exec, &done)) {
+            const cudaError_t e = cudaGraphLaunch(exec, q.stream);
+            if (e == cudaSuccess) {
+                cudaEventRecord(done, q.stream);
+                count_launches(0, 1);
+                if (rts) count_launches(1, 1);
+                count_graph(1);
+                blob_used(slot, q.stream);
+                return true;
+            }
+            cudaGetLastError();   // not launched: launch directly
+            gs_graph_fail<N, R>(key);
+        }
+    }
+
+    const cudaError_t e = enqueue(q.stream, timing_on());
+    count_launches(0, 1);
+    if (rts && e == cudaSuccess) count_launches(1, 1);
     blob_used(slot, q.stream);
     *err = e;
     return true;

@@ -236,7 +236,7 @@ static std::mutex g_mu;
 static void *g_ws[64];
 static size_t g_ws_bytes[64];
 static int *g_status[64];
-static std::atomic<int64_t> g_opt[10] = {1000000000LL, -1, 0, 0, 0, 0, 1, 0, 0, 0};   // KF_OPT_* by index
+static std::atomic<int64_t> g_opt[11] = {1000000000LL, -1, 0, 0, 0, 0, 1, 0, 0, 0, 1};   // KF_OPT_* by index
 
 // KFSCAN_DEBUG=1 in the environment logs each stage of a call to stderr.
 bool debug_on() {
@@ -706,6 +706,7 @@ static kf_status_t run(int op, const kf_model_t *md, int64_t T, const void *y, k
     q.sg_n = g_opt[KF_OPT_SENGUPTA_N].load();
     q.filter_kernel = int(g_opt[KF_OPT_FILTER_KERNEL].load());
     q.rts_kernel = int(g_opt[KF_OPT_RTS_KERNEL].load());
+    q.call_graphs = int(g_opt[KF_OPT_CALL_GRAPHS].load());
     // covariance tables of a time-invariant model (the per-step kernels when
     // the tables do not apply)
     std::shared_ptr<const GainModel> gm;
@@ -969,7 +970,19 @@ static int *noalloc_status_word() {
 
 using namespace kfs;
 
+static std::atomic<int64_t> g_graph_count[2];
+
+void kfs::count_graph(int what) {
+    if (what == 0 || what == 1) g_graph_count[what].fetch_add(1);
+}
+
 extern "C" {
+
+kf_status_t kf_call_graph_stats(int64_t *captured, int64_t *replayed) {
+    if (captured) *captured = g_graph_count[0].load();
+    if (replayed) *replayed = g_graph_count[1].load();
+    return KF_OK;
+}
 
 int kf_bounds_checked(void) {
 #ifdef KF_BOUNDS_CHECK
@@ -1527,9 +1540,10 @@ kf_status_t kf_measure_fma_peak(int fp64, double *flops_per_second) {
 }
 
 kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_COVARIANCE_TABLES) return KF_ERR_ARG;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_CALL_GRAPHS) return KF_ERR_ARG;
     if (opt == KF_OPT_GENERAL_SOLVE && value != 0 && value != 1) return KF_ERR_ARG;
-    if ((opt == KF_OPT_FILTER_KERNEL || opt == KF_OPT_RTS_KERNEL || opt == KF_OPT_COVARIANCE_TABLES) && value != 0 &&
+    if ((opt == KF_OPT_FILTER_KERNEL || opt == KF_OPT_RTS_KERNEL || opt == KF_OPT_COVARIANCE_TABLES ||
+         opt == KF_OPT_CALL_GRAPHS) && value != 0 &&
         value != 1)
         return KF_ERR_ARG;
     if (opt == KF_OPT_SENGUPTA_N && (value < 1 || value > (int64_t(1) << 30) || (value & (value - 1)) != 0))
@@ -1543,7 +1557,7 @@ kf_status_t kf_set_option(kf_option_t opt, int64_t value) {
 }
 
 int64_t kf_get_option(kf_option_t opt) {
-    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_COVARIANCE_TABLES) return -1;
+    if (opt < KF_OPT_WAIT_TIMEOUT_NS || opt > KF_OPT_CALL_GRAPHS) return -1;
     return g_opt[opt].load();
 }
 

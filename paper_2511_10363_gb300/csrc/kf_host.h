@@ -62,6 +62,7 @@ struct LaunchReq {
     int filter_kernel;   // 0: the time-invariant table kernel where it applies, 1: the generic scan kernel
     int rts_kernel;      // 0: the dedicated one-sequence RTS kernel where it applies, 1: the generic scan kernel
     const void *gain;    // covariance tables of a time-invariant model (GainModel), or null
+    int call_graphs;     // 1: repeated covariance-table calls replay a captured CUDA graph
 };
 
 // Device cache of tile-scan tables (kf_api.cu): a table is found by its key,
@@ -94,6 +95,7 @@ bool debug_on();   // KFSCAN_DEBUG set in the environment
 
 // kernel accounting (kf_timing_* in kfscan.h)
 void count_launches(int kind, int n);
+void count_graph(int what);   // call graphs: 0 one captured, 1 one replayed
 bool timing_on();
 void timing_record(int kind, cudaStream_t s, cudaEvent_t *ev);          // start event
 void timing_commit(int kind, cudaStream_t s, cudaEvent_t start);        // stop event

@@ -170,3 +170,43 @@ def test_smoother_below_minimum_length_uses_per_step_kernels():
     y = W.simulate(model, T, seed=5)
     check("rts", model, y, "fp32")
     check("rts", model, y, "fp64")
+
+
+def test_repeated_calls_replay_a_call_graph():
+    """KF_OPT_CALL_GRAPHS (default 1): the second call with the same buffers,
+    length and model captures a graph of the memset and both kernels, later
+    ones replay it.  The replays read the buffers' current contents (the
+    measurements alternate between two sequences), every output matches the
+    oracle, and the same calls with the option at 0 launch directly."""
+    import torch
+    import paper_2511_10363_gb300 as kf
+    model = W.cv_model()
+    T = 30000
+    ys = [oracle_inputs(W.simulate(model, T, seed=s), "fp32") for s in (31, 32)]
+    refs = [oracle_run(model, yo) for yo in ys]
+    yt = torch.empty((T, 2), dtype=torch.float32, device="cuda")
+    ms = torch.empty((T, 4), dtype=torch.float32, device="cuda")
+    Ps = torch.empty((T, 4, 4), dtype=torch.float32, device="cuda")
+    ll = torch.empty(1, dtype=torch.float64, device="cuda")
+    ws = torch.empty(kf.kf_workspace_size("rts", 4, 2, T, "fp32", "auto"), dtype=torch.uint8, device="cuda")
+    for graphs in (1, 0):
+        kf.kf_set_option("call_graphs", graphs)
+        try:
+            s0 = kf.kf_call_graph_stats()
+            for rep in range(3):
+                for yo, ref in zip(ys, refs):
+                    yt.copy_(torch.tensor(yo, dtype=torch.float32))
+                    kf.kf_rts_smooth(model, yt, "fp32", "auto", ms_out=ms, Ps_out=Ps, loglik=ll, workspace=ws)
+                    assert kf.kf_sync_status() == 0
+                    Ps_h = Ps.double().cpu().numpy()
+                    assert mean_err(ms.double().cpu().numpy(), ref["ms_rts"], ref["Ps_rts"]) <= TOL["fp32"]
+                    assert cov_err(Ps_h, ref["Ps_rts"]) <= TOL["fp32"]
+                    assert abs(ll.item() - ref["ll"]) <= 1e-3 * abs(ref["ll"])
+            s1 = kf.kf_call_graph_stats()
+        finally:
+            kf.kf_set_option("call_graphs", 1)
+        if graphs:   # (captured at the second call, unless an earlier test left this key's graph)
+            assert s1["captured"] - s0["captured"] <= 1, (s0, s1)
+            assert s1["replayed"] - s0["replayed"] >= 5, (s0, s1)
+        else:
+            assert s1 == s0
